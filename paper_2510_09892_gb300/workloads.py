@@ -1,0 +1,300 @@
+"""Seeded synthetic inputs for the arc x latitude workloads (host, numpy).
+
+This module draws inputs only: it holds none of the intersection method's
+arithmetic (no normals, no Eq. 2.2). Arcs are built from the great-circle
+parametrisation x(t) = cos(t) a + sin(t) b with orthonormal a, b, which also
+gives an arc's z-range for sampling latitudes inside it. Both the oracle side
+(tests) and the CUDA side (tests, bench) take their inputs from here.
+
+The paper's own datasets (MPFR-sampled latitude bands, and the near-equator
+ill-conditioned set of Sec. 7) are not available; these generators stand in
+for them with the same structure:
+
+* ``uniform_arcs``    endpoints uniform on the sphere, arc length U(0, pi/2),
+                      one latitude drawn uniformly in the arc's z-range
+                      (10^4 arcs: the small parity workload).
+* ``stress_arcs``     the ill-conditioned mix (10^6 arcs): 40 % short arcs
+                      (length log-uniform 1e-10..1e-2 rad), 30 % latitudes
+                      within 1e-12 of the arc's z-extremum (a third of them
+                      in the paper's near-equator band of Sec. 7), 20 %
+                      near-pole arcs (|z| > 1 - 1e-6), 10 % near-antipodal
+                      endpoints.
+* ``mixed_arcs``      90 % uniform + 10 % stress, generated in fixed chunks so
+                      any sample can be regenerated alone (2x10^8 arcs).
+* ``cubed_sphere_edges`` + ``latlon_latitudes`` the regridding workload.
+* ``ragged_meshes``   independent random polygon meshes with per-mesh
+                      latitude grids.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_SEED = 20251009
+CHUNK = 1 << 20  # arcs per independently seeded chunk (mixed_arcs)
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _random_unit(rng, n):
+    return _unit(rng.standard_normal((n, 3)))
+
+
+def _orthonormal_partner(rng, a):
+    """A random unit vector perpendicular to each row of a."""
+    g = rng.standard_normal(a.shape)
+    g -= np.sum(g * a, axis=1, keepdims=True) * a
+    return _unit(g)
+
+
+def _arc_z_range(a, b, L):
+    """z-range of the arc x(t) = cos t a + sin t b, t in [0, L] (L < pi + eps)."""
+    az, bz = a[:, 2], b[:, 2]
+    amp = np.hypot(az, bz)
+    tmax = np.mod(np.arctan2(bz, az), 2 * np.pi)  # z(t) = amp cos(t - tmax)
+    tmin = np.mod(tmax + np.pi, 2 * np.pi)
+    z_end0 = az
+    z_end1 = np.cos(L) * az + np.sin(L) * bz
+    zhi = np.maximum(z_end0, z_end1)
+    zlo = np.minimum(z_end0, z_end1)
+    zhi = np.where(tmax <= L, amp, zhi)
+    zlo = np.where(tmin <= L, -amp, zlo)
+    return zlo, zhi
+
+
+def _arcs_from_length(rng, L):
+    n = L.shape[0]
+    a = _random_unit(rng, n)
+    b = _orthonormal_partner(rng, a)
+    x1 = a
+    x2 = np.cos(L)[:, None] * a + np.sin(L)[:, None] * b
+    return x1, x2, a, b
+
+
+def _z_in_range(rng, a, b, L):
+    zlo, zhi = _arc_z_range(a, b, L)
+    return zlo + rng.random(L.shape[0]) * (zhi - zlo)
+
+
+def uniform_arcs(n: int, seed: int = DEFAULT_SEED):
+    """(A, B, z0): endpoints uniform on S^2, length U(0, pi/2), z0 in the arc's z-range."""
+    rng = np.random.default_rng(seed)
+    L = rng.random(n) * (np.pi / 2)
+    x1, x2, a, b = _arcs_from_length(rng, L)
+    z0 = _z_in_range(rng, a, b, L)
+    return x1, x2, z0
+
+
+def _short(rng, n):
+    L = 10.0 ** rng.uniform(-10, -2, n)
+    x1, x2, a, b = _arcs_from_length(rng, L)
+    return x1, x2, _z_in_range(rng, a, b, L)
+
+
+def _tangent(rng, n):
+    """Arcs containing their highest point; z0 just below it."""
+    n_band = n // 3
+    apex = _random_unit(rng, n)
+    apex[:, 2] = np.abs(apex[:, 2])
+    # the paper's near-equator band (0, 1e-4 deg]: apex latitude in that band
+    band_z = np.sin(np.deg2rad(rng.uniform(1e-7, 1e-4, n_band)))
+    lon = rng.uniform(0, 2 * np.pi, n_band)
+    cz = np.sqrt(1.0 - band_z * band_z)
+    apex[:n_band] = np.stack([cz * np.cos(lon), cz * np.sin(lon), band_z], axis=1)
+    ez = np.array([0.0, 0.0, 1.0])
+    h = _unit(np.cross(np.broadcast_to(ez, apex.shape), apex))  # horizontal tangent
+    t1 = rng.uniform(1e-3, np.pi / 4, n)
+    t2 = rng.uniform(1e-3, np.pi / 4, n)
+    x1 = np.cos(t1)[:, None] * apex - np.sin(t1)[:, None] * h
+    x2 = np.cos(t2)[:, None] * apex + np.sin(t2)[:, None] * h
+    r = 10.0 ** rng.uniform(-16, -12, n)
+    r[:n_band] = apex[:n_band, 2] * 10.0 ** rng.uniform(-15, -2, n_band)
+    z0 = apex[:, 2] - r
+    # half of them mirrored to the southern hemisphere (z -> -z)
+    flip = rng.random(n) < 0.5
+    flip[:n_band] = False
+    for v in (x1, x2):
+        v[flip, 2] = -v[flip, 2]
+    z0[flip] = -z0[flip]
+    return x1, x2, z0
+
+
+def _near_pole(rng, n):
+    def cap_points(m):
+        cz = 1.0 - rng.random(m) * 1e-6
+        sz = np.sqrt((1.0 - cz) * (1.0 + cz))
+        lon = rng.uniform(0, 2 * np.pi, m)
+        return np.stack([sz * np.cos(lon), sz * np.sin(lon), cz], axis=1)
+    x1 = cap_points(n)
+    x2 = cap_points(n)
+    south = rng.random(n) < 0.5
+    x1[south, 2] *= -1
+    x2[south, 2] *= -1
+    z0 = _z_for_endpoints(rng, x1, x2)
+    return x1, x2, z0
+
+
+def _z_for_endpoints(rng, x1, x2):
+    """z0 uniform in the z-range of the minor arc x1 -> x2."""
+    a = _unit(x1)
+    g = x2 - np.sum(x2 * a, axis=1, keepdims=True) * a
+    b = _unit(g)
+    L = np.arctan2(np.linalg.norm(g, axis=1), np.sum(x2 * a, axis=1))
+    return _z_in_range(rng, a, b, L)
+
+
+def _antipodal(rng, n):
+    x1 = _random_unit(rng, n)
+    d = _random_unit(rng, n) * (10.0 ** rng.uniform(-12, -4, n))[:, None]
+    x2 = _unit(-x1 + d)
+    z0 = _z_for_endpoints(rng, x1, x2)
+    return x1, x2, z0
+
+
+STRESS_CLASSES = (("short", 0.4), ("tangent", 0.3), ("pole", 0.2), ("antipodal", 0.1))
+
+
+def stress_arcs(n: int, seed: int = DEFAULT_SEED + 1, return_class: bool = False):
+    """Ill-conditioned mix: 40 % short, 30 % near-tangent, 20 % near-pole, 10 % near-antipodal."""
+    rng = np.random.default_rng(seed)
+    counts = [int(round(n * w)) for _, w in STRESS_CLASSES]
+    counts[0] += n - sum(counts)
+    makers = {"short": _short, "tangent": _tangent, "pole": _near_pole, "antipodal": _antipodal}
+    parts, cls = [], []
+    for (name, _), m in zip(STRESS_CLASSES, counts):
+        if m > 0:
+            parts.append(makers[name](rng, m))
+            cls.append(np.full(m, [c for c, _ in STRESS_CLASSES].index(name), dtype=np.int8))
+    x1 = np.concatenate([p[0] for p in parts])
+    x2 = np.concatenate([p[1] for p in parts])
+    z0 = np.concatenate([p[2] for p in parts])
+    klass = np.concatenate(cls)
+    perm = rng.permutation(n)
+    out = (np.ascontiguousarray(x1[perm]), np.ascontiguousarray(x2[perm]),
+           np.ascontiguousarray(z0[perm]))
+    if return_class:
+        return out + (klass[perm],)
+    return out
+
+
+def mixed_chunk(k: int, seed: int = DEFAULT_SEED + 4, size: int = CHUNK):
+    """Chunk k of the 90/10 uniform/stress mix (regenerable on its own)."""
+    ss = np.random.SeedSequence([seed, k])
+    s_uni, s_str, s_mix = ss.generate_state(3)
+    n_str = size // 10
+    u = uniform_arcs(size - n_str, seed=int(s_uni))
+    s = stress_arcs(n_str, seed=int(s_str))
+    perm = np.random.default_rng(int(s_mix)).permutation(size)
+    return tuple(np.ascontiguousarray(np.concatenate([a, b])[perm]) for a, b in zip(u, s))
+
+
+def mixed_arcs(n: int, seed: int = DEFAULT_SEED + 4):
+    """n arcs of the 90/10 mix, as consecutive chunks of CHUNK arcs."""
+    A = np.empty((n, 3))
+    B = np.empty((n, 3))
+    z = np.empty(n)
+    for k in range((n + CHUNK - 1) // CHUNK):
+        lo, hi = k * CHUNK, min(n, (k + 1) * CHUNK)
+        a, b, c = mixed_chunk(k, seed)
+        A[lo:hi], B[lo:hi], z[lo:hi] = a[:hi - lo], b[:hi - lo], c[:hi - lo]
+    return A, B, z
+
+
+# ------------------------------------------------------------------ meshes --
+def cubed_sphere_edges(N: int):
+    """Edges of an equiangular gnomonic cubed sphere with N x N cells per face.
+
+    Each face contributes N(N+1) edges along each grid direction, so the mesh
+    has 12 N (N+1) edges (face-boundary edges appear once per adjacent face).
+    Returns (A, B) as (E, 3) arrays of unit vectors.
+    """
+    ang = -np.pi / 4 + (np.pi / 2) * np.arange(N + 1) / N
+    t = np.tan(ang)
+    u, v = np.meshgrid(t, t, indexing="ij")  # (N+1, N+1)
+    one = np.ones_like(u)
+    faces = [(one, u, v), (-one, -u, v), (-u, one, v), (u, -one, v), (-v, u, one), (v, u, -one)]
+    A_parts, B_parts = [], []
+    for fx, fy, fz in faces:
+        P = _unit(np.stack([fx, fy, fz], axis=-1))  # (N+1, N+1, 3)
+        A_parts += [P[:-1, :, :].reshape(-1, 3), P[:, :-1, :].reshape(-1, 3)]
+        B_parts += [P[1:, :, :].reshape(-1, 3), P[:, 1:, :].reshape(-1, 3)]
+    return (np.ascontiguousarray(np.concatenate(A_parts)),
+            np.ascontiguousarray(np.concatenate(B_parts)))
+
+
+def latlon_latitudes(n_lat: int):
+    """z of n_lat equally spaced latitudes from -90 to +90 degrees (ascending)."""
+    deg = -90.0 + 180.0 * np.arange(n_lat) / (n_lat - 1)
+    z = np.sin(np.deg2rad(deg))
+    z[0], z[-1] = -1.0, 1.0
+    return z
+
+
+def _fibonacci_points(m):
+    i = np.arange(m) + 0.5
+    z = 1.0 - 2.0 * i / m
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * np.pi * (3.0 - math.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def polygon_mesh(rng, n_edges: int):
+    """Independent small polygons (3-12 vertices) around jittered Fibonacci points.
+
+    Returns (A, B) edge endpoint arrays with exactly n_edges rows.
+    """
+    kmean = 7.5
+    m = max(1, int(math.ceil(n_edges / kmean)))
+    centres = _fibonacci_points(m)
+    spacing = math.sqrt(4 * math.pi / m)
+    centres = _unit(centres + 0.3 * spacing * rng.standard_normal((m, 3)))
+    k = rng.integers(3, 13, m)
+    tot = int(k.sum())
+    while tot < n_edges:  # top up with more polygons if the draw fell short
+        extra = rng.integers(3, 13, 8)
+        k = np.concatenate([k, extra])
+        centres = np.concatenate([centres, _random_unit(rng, 8)])
+        tot = int(k.sum())
+    # tangent frame at each centre
+    e1 = _orthonormal_partner(rng, centres)
+    e2 = np.cross(centres, e1)
+    poly = np.repeat(np.arange(k.size), k)
+    first = np.concatenate([[0], np.cumsum(k)[:-1]])
+    j = np.arange(tot) - first[poly]
+    ang = 2 * np.pi * (j + 0.3 * rng.random(tot)) / k[poly]
+    rad = 0.5 * spacing
+    V = _unit(centres[poly] + rad * (np.cos(ang)[:, None] * e1[poly] + np.sin(ang)[:, None] * e2[poly]))
+    nxt = np.where(j + 1 == k[poly], first[poly], np.arange(tot) + 1)
+    A = V[:n_edges]
+    B = V[nxt][:n_edges]
+    return np.ascontiguousarray(A), np.ascontiguousarray(B)
+
+
+def ragged_meshes(n_mesh: int, e_min: float, e_max: float, seed: int = DEFAULT_SEED + 3,
+                  lat_min: int = 180, lat_max: int = 2881):
+    """A batch of independent polygon meshes with per-mesh latitude grids.
+
+    Edge counts are log-uniform in [e_min, e_max]; latitude counts uniform in
+    [lat_min, lat_max]. Returns dict with A, B (E,3), edge_offsets (M+1,),
+    lat_z (sum L,), lat_offsets (M+1,).
+    """
+    rng = np.random.default_rng(seed)
+    E = np.exp(rng.uniform(math.log(e_min), math.log(e_max), n_mesh)).astype(np.int64)
+    E = np.maximum(E, 1)
+    L = rng.integers(lat_min, lat_max + 1, n_mesh)
+    A_parts, B_parts, Z_parts = [], [], []
+    for m in range(n_mesh):
+        a, b = polygon_mesh(rng, int(E[m]))
+        A_parts.append(a)
+        B_parts.append(b)
+        Z_parts.append(latlon_latitudes(int(L[m])))
+    edge_offsets = np.concatenate([[0], np.cumsum(E)]).astype(np.int64)
+    lat_offsets = np.concatenate([[0], np.cumsum(L)]).astype(np.int64)
+    return {"A": np.ascontiguousarray(np.concatenate(A_parts)),
+            "B": np.ascontiguousarray(np.concatenate(B_parts)),
+            "edge_offsets": edge_offsets,
+            "lat_z": np.ascontiguousarray(np.concatenate(Z_parts)),
+            "lat_offsets": lat_offsets}
