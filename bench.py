@@ -1,0 +1,407 @@
+"""Benchmark: arc x constant-latitude intersections on one or more GB300s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sphx|reference]
+
+A step is one dense call (sphx_intersect_gca_constlat, FP64-EFT) over the
+ill-conditioned workload of 10^6 arcs (40 % short, 30 % near-tangent, 20 %
+near-pole, 10 % near-antipodal), inputs resident in HBM; the L2 cache is
+flushed (a 256 MiB write) between timed steps. Direct FP64 and float-float are
+timed the same way beside it. Under torchrun each rank runs its own
+independently seeded batch (weak scaling, no data-path collective); the step
+time is the maximum over ranks.
+
+``--impl reference`` times the exact-rational CPU oracle, as it stands, on
+the host's cores over bounded samples of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2510_09892_gb300 import workloads as W  # noqa: E402
+
+METRIC = "arc–latitude intersections/sec at ≤4-ulp error, EFT vs direct FP64, % HBM roofline"
+UNIT = "intersections/s"
+N_ARCS = 1_000_000
+WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-uniform 1e-10..1e-2 rad), "
+            "30% nearly tangent (z0 within 1e-12 of the z-extremum), 20% near-pole "
+            "(|z| > 1-1e-6), 10% near-antipodal")
+# algorithmic work per arc of the dense call (both roots and the on-arc test)
+BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
+FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
+L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE = 32_768            # arcs per oracle step
+
+
+# ------------------------------------------------------------- host logic --
+def dist_env():
+    """(rank, world, local_rank) from the torchrun environment (1 process if unset)."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Seed of rank's batch: rank 0 runs the published workload seed itself."""
+    return base if rank == 0 else int(np.random.SeedSequence([base, rank]).generate_state(1)[0])
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Maximum of a float over all ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 100 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        # wait (at most 3 s) for the first sample so the timed region is covered
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 3.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ reference arm --
+def oracle_rate(A, B, z, pool) -> float:
+    """Arcs per second of the exact oracle over the given arcs, on the pool."""
+    from oracle import exact
+    n = len(z)
+    chunk = max(1, n // (4 * pool._processes))
+    jobs = [(A[i:i + chunk].tolist(), B[i:i + chunk].tolist(), z[i:i + chunk].tolist())
+            for i in range(0, n, chunk)]
+    t0 = time.perf_counter()
+    pool.map(exact._batch_worker, jobs)
+    return n / (time.perf_counter() - t0)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    A, B, z = W.stress_arcs(N_ARCS)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        rates = []
+        for step in range(args.warmup + args.steps):
+            lo = (step * CPU_SAMPLE) % (N_ARCS - CPU_SAMPLE)
+            r = oracle_rate(A[lo:lo + CPU_SAMPLE], B[lo:lo + CPU_SAMPLE], z[lo:lo + CPU_SAMPLE],
+                            pool)
+            if step >= args.warmup:
+                rates.append(r)
+    value = CPU_SAMPLE / statistics.mean([CPU_SAMPLE / r for r in rates])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * CPU_SAMPLE / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "exact rational (Python int), rounded to f64",
+        "data": "synthetic", "config": config_dict(args, "eft"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{CPU_SAMPLE} consecutive arcs of the workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, mode):
+    return {"workload": WORKLOAD, "arcs_per_gpu": N_ARCS, "mode": mode,
+            "seed": W.DEFAULT_SEED + 1, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"independent batches, {args.gpus} GPU(s)"}
+
+
+# ------------------------------------------------------------------ GPU arm --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sphx", choices=["sphx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    # the oracle's process pool starts before CUDA does ('spawn' regardless)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg()
+
+    import torch
+    import torch.distributed as dist
+    from paper_2510_09892_gb300 import sphx
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    A, B, z = W.stress_arcs(N_ARCS, seed=shard_seed(W.DEFAULT_SEED + 1, rank))
+    tA, tB, tz = (torch.from_numpy(v).to(dev) for v in (A, B, z))
+    pts = torch.empty((N_ARCS, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.empty((N_ARCS,), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(mode, steps, warmup):
+        """Mean kernel time (ms) of `steps` dense calls, L2 flushed before each."""
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(warmup + steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, mode, stream)
+                e1.record(stream)
+                if i >= warmup:
+                    ms.append((e0, e1))
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in ms]
+
+    fp64_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP64) / 2  # FMA/s = FP64 op slots/s
+    fp32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP32) / 2
+    int32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_INT32)
+
+    # warm-up of every mode, then the headline timed region
+    for mode in ("eft", "direct", "ff32"):
+        timed(mode, 1, args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+    # the sampler runs through every timed leg (headline, other modes, e2e)
+    with ClockSampler(local) as clocks:
+        t_wall = time.perf_counter()
+        eft_ms = timed("eft", args.steps, 0)
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+        gpu_launches = args.steps  # one dense_kernel launch per step
+        step_ms = reduce_max(statistics.mean(eft_ms), dev)
+        value = world * N_ARCS / (step_ms * 1e-3)
+
+        modes = {}
+        for mode in ("direct", "ff32"):
+            m = reduce_max(statistics.mean(timed(mode, args.steps, 0)), dev)
+            modes[mode] = {"value": world * N_ARCS / (m * 1e-3), "ms_per_step": m}
+        modes["eft"] = {"value": value, "ms_per_step": step_ms}
+        e2e = e2e_leg(sphx, torch, dev, A, B, z, args)
+        # the timed legs last well under a second, shorter than the sampling
+        # period: keep the same kernel running for 1.5 s more so that the
+        # clock samples describe the GPU under this load (not timed)
+        soak_end = time.perf_counter() + 1.5
+        while time.perf_counter() < soak_end:
+            timed("eft", 50, 0)
+    clk = clocks.summary()
+    clk["window"] = "timed legs plus a 1.5 s soak of the same kernel right after"
+
+    # hits per step, from one more EFT call's outputs
+    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "eft")
+    hits = int(torch.clamp(cnt, min=0).sum().item())
+
+    kernel_ms = statistics.mean(eft_ms)
+    fp64_ops = FP64_OPS_PER_ARC["eft"] * N_ARCS
+    roofline = {
+        "bound": "alu", "unit": "TFLOP/s",
+        "achieved": fp64_ops / (kernel_ms * 1e-3) / 1e12,
+        "peak": fp64_peak / 1e12,
+        "frac": (fp64_ops / (kernel_ms * 1e-3)) / fp64_peak,
+        "traffic": None,
+        "kernel": "dense_kernel<EFT_FP64>",
+        "note": ("FP64 pipe: algorithmic FP64 operations (add, mul, fma, div, sqrt each one "
+                 "op, 465 per arc) per second against the measured FP64 FMA issue rate "
+                 "(sphx_probe_fma_rate, live, of measured)"),
+    }
+    hbm_peak = measured_hbm_peak()
+    roofline_hbm = {
+        "bound": "hbm", "unit": "GB/s",
+        "achieved": BYTES_PER_ARC * N_ARCS / (kernel_ms * 1e-3) / 1e9,
+        "peak": hbm_peak, "frac": BYTES_PER_ARC * N_ARCS / (kernel_ms * 1e-3) / 1e9 / hbm_peak,
+        "note": "108 B per arc (56 in, 52 out) against the measured copy bandwidth",
+    }
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, "eft"), "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clk, "roofline": roofline, "roofline_hbm": roofline_hbm,
+        "modes": modes, "eft_over_direct_time": step_ms / modes["direct"]["ms_per_step"],
+        "hits_per_step": hits, "timed_wall_s": t_wall,
+        "peaks": {"fp64_fma_per_s": fp64_peak, "fp32_fma_per_s": fp32_peak,
+                  "int32_imad_per_s": int32_peak, "hbm_gbs": hbm_peak},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measured_hbm_peak() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0  # fallback figure of the profiling recipe
+
+
+def cpu_baseline_leg() -> dict:
+    """The exact oracle, as it stands, on all host cores over a bounded sample."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = min(N_ARCS, 6000 * cores)  # ~0.6 s of oracle work per core
+    A, B, z = W.stress_arcs(N_ARCS)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        oracle_rate(A[:1024], B[:1024], z[:1024], pool)  # start the workers
+        rate = oracle_rate(A[:n], B[:n], z[:n], pool)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} arcs of the 10^6-arc stress workload"}
+
+
+def e2e_leg(sphx, torch, dev, A, B, z, args) -> dict:
+    """Same metric through the C ABI from pinned HOST buffers: every step copies
+    the inputs in and the points and counts out, in 4 chunks over 2 streams so
+    the copies overlap the kernels."""
+    n = len(z)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hz = torch.from_numpy(z).pin_memory()
+    hP = torch.empty((n, 2, 3), dtype=torch.float64).pin_memory()
+    hC = torch.empty((n,), dtype=torch.int32).pin_memory()
+    chunks = 4
+    step = (n + chunks - 1) // chunks
+    step = (step + 127) // 128 * 128
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    bufs = []
+    for i in range(2):
+        bufs.append((torch.empty((step, 3), dtype=torch.float64, device=dev),
+                     torch.empty((step, 3), dtype=torch.float64, device=dev),
+                     torch.empty((step,), dtype=torch.float64, device=dev),
+                     torch.empty((step, 2, 3), dtype=torch.float64, device=dev),
+                     torch.empty((step,), dtype=torch.int32, device=dev)))
+
+    def one_step():
+        for c in range(chunks):
+            lo, hi = c * step, min(n, (c + 1) * step)
+            if lo >= hi:
+                break
+            m = hi - lo
+            s = streams[c % 2]
+            dA, dB, dz, dP, dC = bufs[c % 2]
+            with torch.cuda.stream(s):
+                dA[:m].copy_(hA[lo:hi], non_blocking=True)
+                dB[:m].copy_(hB[lo:hi], non_blocking=True)
+                dz[:m].copy_(hz[lo:hi], non_blocking=True)
+                sphx.sphx_intersect_gca_constlat(dA[:m], dB[:m], dz[:m], dP[:m], dC[:m], "eft", s)
+                hP[lo:hi].copy_(dP[:m], non_blocking=True)
+                hC[lo:hi].copy_(dC[:m], non_blocking=True)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream(dev)
+    e0.record(cur)
+    for s in streams:
+        s.wait_stream(cur)
+    for _ in range(args.steps):
+        one_step()
+    for s in streams:
+        cur.wait_stream(s)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = reduce_max(ms, dev)
+    _, world, _ = dist_env()
+    return {"value": world * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": n * 56, "d2h_bytes_per_step": n * 52}
+
+
+if __name__ == "__main__":
+    main()

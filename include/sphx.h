@@ -1,0 +1,183 @@
+/*
+ * sphx -- great-circle arc x constant-latitude intersection on the GPU.
+ *
+ * C ABI of libsphx.so. Every compute call is stream ordered and returns once
+ * its work is enqueued; pointers are caller-owned device pointers unless a
+ * comment says "host". Errors found before a launch come back as the return
+ * value and nothing is launched; errors found on the device (output capacity,
+ * a bounded wait that ran out) are recorded in the context's device status
+ * word and reported by sphx_sync_status().
+ *
+ * The problem (Sec. 1.2 of Chen, Ullrich, Panetta, "Fast and Accurate
+ * Intersections on a Sphere", arXiv 2510.09892): an arc is the shorter great
+ * circle arc between two FP64 points x1, x2 (not necessarily of unit norm:
+ * the formula only uses the direction of n = x1 x x2); a latitude is the plane
+ * z = z0. The candidate points are Eq. 2.2,
+ *   P = ( -(z0 nx nz +- s ny) / |n_xy|^2, -(z0 ny nz -+ s nx) / |n_xy|^2, z0 ),
+ *   s = sqrt(|n_xy|^2 - |n|^2 z0^2),
+ * they exist iff |n_xy|^2 >= |n|^2 z0^2 (two when strict, Sec. 2), and a
+ * candidate is a hit iff it lies on the arc, decided as (x1 x P).n >= 0 and
+ * (P x x2).n >= 0 (the paper only requires "between x1 and x2").
+ * Root slot 0 is the upper sign (the alpha* <= 0 root that Algorithm 8,
+ * AccuX, returns); slot 1 the lower sign. A tangent point (s = 0) is one hit
+ * in slot 0.
+ */
+#ifndef SPHX_H
+#define SPHX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* a cudaStream_t (NULL = the legacy default stream) */
+typedef struct CUstream_st *sphx_stream;
+
+typedef enum {
+    SPHX_OK = 0,
+    SPHX_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or enum: nothing launched */
+    SPHX_ERR_CUDA = 2,        /* a CUDA runtime call failed (see sphx_last_cuda_error) */
+    SPHX_ERR_CAPACITY = 3,    /* ragged output needed more records than out_cap */
+    SPHX_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    SPHX_ERR_NOMEM = 5,       /* scratch allocation failed */
+    SPHX_ERR_UNSUPPORTED = 6  /* no sm_103a device, or a feature not built */
+} sphx_status;
+
+/* How the candidate points are evaluated. */
+typedef enum {
+    /* Eq. 2.2 translated directly into FP64 (Sec. 4): plain cross product,
+       sums of squares, sqrt and two divisions, no FMA contraction. */
+    SPHX_MODE_DIRECT_FP64 = 0,
+    /* AccuX (Algorithm 8) in FP64 with error-free transformations, both
+       roots, each AccuDOP pair renormalised by one TwoSum so that the
+       compensation terms stay below u times their leading parts (needed by
+       SumOfSquaresC for arcs much shorter than 1e-8 rad or nearly antipodal).
+       Error <= 4 ulp per component of the correctly rounded exact point. */
+    SPHX_MODE_EFT_FP64 = 1,
+    /* float-float: the normal by FP64 AccuDOP, rescaled by an exact power of
+       two; squared norms, s^2, s and the numerators in pairs of FP32 with
+       TwoSum / FMA TwoProd; the final divisions and the containment test in
+       FP64. s^2 carries about 48 bits, so the error grows near tangency and
+       near the poles: |P~ - P| <= 2 (2^-44 sqrt(1 - z0^2)
+       + 2^-48 |n|^2 / (|n_xy| s)); hit counts can differ from the exact ones
+       where s^2 is below that resolution. */
+    SPHX_MODE_EFT_FF32 = 2,
+    /* Algorithm 8 exactly as printed (no renormalisation after AccuDOP), for
+       comparison; loses accuracy on very short and near-antipodal arcs. */
+    SPHX_MODE_EFT_FP64_PRINTED = 3
+} sphx_mode;
+
+/* Output compaction scheme of the ragged call. */
+typedef enum {
+    SPHX_COMPACT_AUTO = 0,    /* autotuned choice, else ATOMIC */
+    SPHX_COMPACT_ATOMIC = 1,  /* one atomicAdd per warp: record order unspecified */
+    SPHX_COMPACT_ORDERED = 2  /* decoupled look-back: records in (edge, lat, root) order */
+} sphx_compaction;
+
+typedef struct sphx_context sphx_context;
+
+/* One compacted hit of the ragged call: 32 bytes. */
+typedef struct {
+    int64_t edge; /* global edge index into A, B */
+    int32_t lat;  /* index into the concatenated lat_z array */
+    int32_t root; /* 0 or 1: root slot of Eq. 2.2 as above */
+    double x, y;  /* P_x, P_y; P_z is lat_z[lat] */
+} sphx_hit;
+
+/* Launch-shape overrides for the ragged path (0 = autotuned / default). */
+typedef struct {
+    int32_t threads_per_block; /* 64..1024, multiple of 32 */
+    int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SM count */
+    int32_t pairs_per_lane;    /* candidate pairs a lane takes per claimed chunk */
+    int32_t compaction;        /* sphx_compaction */
+    int32_t use_graph;         /* 1: capture the ragged launch sequence in a CUDA graph */
+} sphx_tuning;
+
+/* Create a context on `device` (made current). The context owns the scratch
+   of the ragged call, its device status word, the tuning cache and the CUDA
+   graphs. Returns SPHX_ERR_UNSUPPORTED if the device is not compute 10.3. */
+sphx_status sphx_create(sphx_context **ctx, int device);
+void sphx_destroy(sphx_context *ctx);
+
+/* Dense call: arc i = (A[i], B[i]) against latitude z0[i], i < n.
+   A, B: device, n x 3 row-major FP64 (a torch (n, 3) tensor), 16-byte aligned.
+   z0: device, n FP64. out_pts: device, n x 2 x 3 FP64, slot r of arc i at
+   out_pts[6i + 3r .. 6i + 3r + 2]; slots without a hit are NaN.
+   out_count: device, n int32: number of hits 0..2, or -1 when the arc is
+   degenerate (computed n = 0) or lies on the equator with z0 = 0 (coincident
+   circles). Non-finite inputs give count 0. n = 0 is a no-op.
+   Allocates nothing; safe to capture in a CUDA graph. */
+sphx_status sphx_intersect_gca_constlat(const double *A, const double *B, const double *z0,
+                                        int64_t n, double *out_pts, int32_t *out_count,
+                                        sphx_mode mode, sphx_stream stream);
+
+/* Candidate latitude ranges of a ragged batch (step a11 of the hot path):
+   for each edge e of mesh m, [lo[e], hi[e]) indexes lat_z (global indices)
+   and covers every latitude of mesh m inside the edge's z-range (the endpoint
+   z's and, when the arc passes it, the arc's apex |n_xy| / |n|), widened by
+   1e-13 so that no hit is lost to rounding. lat_z must be sorted ascending
+   within each mesh. Sizes as in sphx_intersect_ragged. lo, hi: device int32[E]. */
+sphx_status sphx_candidate_ranges(const double *A, const double *B, const int64_t *edge_offsets,
+                                  int32_t M, int64_t E, const double *lat_z,
+                                  const int64_t *lat_offsets, int64_t L, int32_t *lo,
+                                  int32_t *hi, sphx_stream stream);
+
+/* Ragged call: M meshes; mesh m owns edges [edge_offsets[m], edge_offsets[m+1])
+   of A, B (device, E x 3 FP64) and latitudes [lat_offsets[m], lat_offsets[m+1])
+   of lat_z (device, L FP64, ascending within each mesh). edge_offsets and
+   lat_offsets are device int64[M + 1] starting at 0 and ending at E and L.
+   Every edge is tested against every latitude of its mesh in its z-range:
+   edge_lat_lo / edge_lat_hi (device int32[E], global latitude indices) give
+   those ranges, or both NULL to compute them (sphx_candidate_ranges).
+   Hits are written as sphx_hit records to out (device, out_cap records);
+   *out_total (device int64) receives the number of hits. If it exceeds
+   out_cap, only out_cap records are written and sphx_sync_status() reports
+   SPHX_ERR_CAPACITY. Degenerate pairs (count -1 in the dense call) give no
+   record. Scratch comes from the context (allocated on the first call for a
+   given size, then reused); the launch sequence is captured in a CUDA graph
+   on the first call with a given argument set and replayed afterwards.
+   Calls on one context must not overlap in time. */
+sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const double *B,
+                                  const int64_t *edge_offsets, int32_t M, int64_t E,
+                                  const double *lat_z, const int64_t *lat_offsets, int64_t L,
+                                  const int32_t *edge_lat_lo, const int32_t *edge_lat_hi,
+                                  sphx_mode mode, sphx_hit *out, int64_t out_cap,
+                                  int64_t *out_total, sphx_stream stream);
+
+/* Synchronise `stream`, read and clear the context's device status word.
+   Returns SPHX_OK, SPHX_ERR_CAPACITY or SPHX_ERR_TIMEOUT (or SPHX_ERR_CUDA). */
+sphx_status sphx_sync_status(sphx_context *ctx, sphx_stream stream);
+
+/* Fix (tuning != NULL) or release (NULL) the ragged launch shape. */
+sphx_status sphx_set_tuning(sphx_context *ctx, const sphx_tuning *tuning);
+/* Read the tuning the next ragged call will use. */
+sphx_status sphx_get_tuning(sphx_context *ctx, sphx_tuning *tuning);
+
+/* Autotune the ragged launch shape on the given batch (same arguments as
+   sphx_intersect_ragged): times each candidate shape with CUDA events and
+   keeps the fastest for this context. Synchronises `stream`. If ms_out is not
+   NULL (host), it receives the best time in milliseconds. The trial runs
+   write out and *out_total; any status they raise (such as a capacity
+   overflow) is cleared before returning. */
+sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const double *B,
+                                 const int64_t *edge_offsets, int32_t M, int64_t E,
+                                 const double *lat_z, const int64_t *lat_offsets, int64_t L,
+                                 sphx_mode mode, sphx_hit *out, int64_t out_cap,
+                                 int64_t *out_total, sphx_stream stream, double *ms_out);
+
+/* Peak probe of the current device, written to *rate (host); synchronises
+   the device. pipe = 0: FP32 FMA, 1: FP64 FMA, in floating-point operations
+   per second (an FMA counts 2); pipe = 2: 32-bit integer multiply-adds per
+   second. Independent chains, 8 per thread, 8 blocks of 256 threads per SM. */
+sphx_status sphx_probe_fma_rate(int pipe, double *rate);
+
+/* Error text of a status; the last CUDA error string seen by the library. */
+const char *sphx_status_string(sphx_status status);
+const char *sphx_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHX_H */

@@ -1,0 +1,101 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sphx.h"
+
+namespace sphx {
+
+// device status word bits (OR-ed by kernels, read by sphx_sync_status)
+enum : unsigned { kStatusCapacity = 1u, kStatusTimeout = 2u, kStatusScratch = 4u };
+
+// bound on the ordered compaction's look-back spin: each iteration is one L2
+// read plus a 64 ns sleep (~0.5 us), so the wait gives up after about a second
+constexpr long long kSpinLimit = 2000000;
+
+void set_cuda_error(cudaError_t e);
+
+#define SPHX_CUDA(call)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            ::sphx::set_cuda_error(e_);                  \
+            return SPHX_ERR_CUDA;                        \
+        }                                                \
+    } while (0)
+
+// launch shape of the ragged intersection kernel
+struct RaggedShape {
+    int threads = 256;
+    int blocks_per_sm = 4;
+    int pairs_per_lane = 2;
+    int compaction = SPHX_COMPACT_ATOMIC;
+    int use_graph = 1;
+    bool operator<(const RaggedShape &o) const {
+        return std::tie(threads, blocks_per_sm, pairs_per_lane, compaction, use_graph) <
+               std::tie(o.threads, o.blocks_per_sm, o.pairs_per_lane, o.compaction, o.use_graph);
+    }
+};
+
+// scratch buffers of one ragged argument set
+struct RaggedScratch {
+    int32_t *lo = nullptr, *hi = nullptr;  // computed candidate ranges (E each)
+    long long *offsets = nullptr;          // exclusive scan of hi - lo, E + 1
+    long long *block_sums = nullptr;       // per scan block, nb + 1
+    unsigned long long *ring = nullptr;    // look-back ring (ORDERED)
+    unsigned long long *counters = nullptr;  // [0] chunk ticket, [1] output cursor
+    int64_t E = -1, nb = 0, ring_slots = 0;
+};
+
+// argument block of the persistent ragged kernel
+struct RaggedArgs {
+    const double *A, *B, *lat_z;
+    const int32_t *lo;
+    const long long *offsets;  // E + 1 entries: exclusive scan of candidate counts
+    int64_t E, L;
+    sphx_hit *out;
+    int64_t cap;
+    unsigned long long *out_total;
+    unsigned long long *counters;  // [0] chunk ticket
+    unsigned long long *ring;      // look-back ring (ORDERED)
+    int64_t ring_slots;            // power of two
+    unsigned *status;
+};
+
+// ragged.cu
+int64_t scan_blocks_for(int64_t E);
+cudaError_t launch_candidates(const double *A, const double *B, const int64_t *edge_offsets,
+                              int M, int64_t E, const double *lat_z, int64_t L,
+                              const int64_t *lat_offsets, int32_t *lo, int32_t *hi,
+                              int sm_count, cudaStream_t s);
+cudaError_t launch_scan(const int32_t *lo, const int32_t *hi, int64_t E, long long *block_sums,
+                        long long *offsets, cudaStream_t s);
+cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, int sm_count,
+                          cudaStream_t s);
+
+struct GraphKey {
+    std::vector<uintptr_t> v;
+    bool operator<(const GraphKey &o) const { return v < o.v; }
+};
+
+}  // namespace sphx
+
+struct sphx_context {
+    int device = 0;
+    int sm_count = 0;
+    unsigned *status = nullptr;  // device status word
+    cudaStream_t capture_stream = nullptr;
+    sphx::RaggedScratch scratch;
+    bool tuned = false;          // tuning fixed by sphx_set_tuning / autotune
+    sphx::RaggedShape shape;
+    std::map<sphx::GraphKey, cudaGraphExec_t> graphs;
+    std::mutex mu;
+};

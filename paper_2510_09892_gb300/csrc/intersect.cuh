@@ -1,0 +1,289 @@
+// Per-pair intersection of one great circle arc (x1, x2) with one latitude
+// z = z0: Eq. 2.2 of arXiv 2510.09892 evaluated three ways (direct FP64,
+// AccuX in FP64, float-float), followed by the on-arc test.
+//
+// Conventions (shared by every mode):
+//   count = -1  computed n = 0 (x1 parallel to x2), or n_xy = 0 and z0 = 0
+//               (the arc lies on the equator: coincident circles);
+//   count = 0   no hit, also for any non-finite input and for n_xy = 0,
+//               z0 != 0 (parallel planes);
+//   slot 0      the upper sign of Eq. 2.2 (the alpha* <= 0 root that
+//               Algorithm 8 returns), slot 1 the lower sign;
+//   tangency    computed s^2 == 0 gives one candidate, in slot 0;
+//   on-arc      with m1 = n x x1 and m2 = x2 x n, a candidate P is kept iff
+//               P . m1 >= 0 and P . m2 >= 0 (that is (x1 x P).n >= 0 and
+//               (P x x2).n >= 0: P between x1 and x2 on the minor arc).
+#pragma once
+#include "eft.cuh"
+
+namespace sphx {
+
+enum : int { kDirect = 0, kEftFp64 = 1, kEftFf32 = 2, kEftFp64Printed = 3 };
+
+struct PairOut {
+    int count;      // -1, 0, 1, 2
+    bool hit[2];    // slot r holds a hit
+    double px[2], py[2];
+};
+
+__device__ __forceinline__ bool finite7(const double (&x1)[3], const double (&x2)[3], double z0) {
+    return isfinite(x1[0]) && isfinite(x1[1]) && isfinite(x1[2]) && isfinite(x2[0]) &&
+           isfinite(x2[1]) && isfinite(x2[2]) && isfinite(z0);
+}
+
+__device__ __forceinline__ void clear(PairOut &o, int count) {
+    o.count = count;
+    o.hit[0] = o.hit[1] = false;
+    o.px[0] = o.px[1] = o.py[0] = o.py[1] = 0.0;
+}
+
+// ---- Sec. 4: direct FP64 translation of Eq. 2.2 (no FMA anywhere) -----------
+__device__ __forceinline__ void pair_direct(const double (&x1)[3], const double (&x2)[3],
+                                            double z0, PairOut &o) {
+    if (!finite7(x1, x2, z0)) return clear(o, 0);
+    double nx = sub(mul(x1[1], x2[2]), mul(x1[2], x2[1]));
+    double ny = sub(mul(x1[2], x2[0]), mul(x1[0], x2[2]));
+    double nz = sub(mul(x1[0], x2[1]), mul(x1[1], x2[0]));
+    double S2 = add(mul(nx, nx), mul(ny, ny));
+    double S3 = add(S2, mul(nz, nz));
+    if (S3 == 0.0) return clear(o, -1);
+    if (S2 == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
+    double s2 = sub(S2, mul(S3, mul(z0, z0)));
+    if (!(s2 >= 0.0)) return clear(o, 0);
+    double s = sqrt_(s2);
+    double a = mul(mul(z0, nx), nz);
+    double b = mul(mul(z0, ny), nz);
+    double sny = mul(s, ny), snx = mul(s, nx);
+    double m1x = sub(mul(ny, x1[2]), mul(nz, x1[1]));
+    double m1y = sub(mul(nz, x1[0]), mul(nx, x1[2]));
+    double m1z = sub(mul(nx, x1[1]), mul(ny, x1[0]));
+    double m2x = sub(mul(x2[1], nz), mul(x2[2], ny));
+    double m2y = sub(mul(x2[2], nx), mul(x2[0], nz));
+    double m2z = sub(mul(x2[0], ny), mul(x2[1], nx));
+    const int nroots = s2 > 0.0 ? 2 : 1;
+    o.count = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o.hit[r] = false;
+        if (r >= nroots) continue;
+        double X = r == 0 ? add(a, sny) : sub(a, sny);
+        double Y = r == 0 ? sub(b, snx) : add(b, snx);
+        double Px = -div_(X, S2);
+        double Py = -div_(Y, S2);
+        double t1 = add(add(mul(Px, m1x), mul(Py, m1y)), mul(z0, m1z));
+        double t2 = add(add(mul(Px, m2x), mul(Py, m2y)), mul(z0, m2z));
+        o.px[r] = Px;
+        o.py[r] = Py;
+        if (t1 >= 0.0 && t2 >= 0.0) {
+            o.hit[r] = true;
+            ++o.count;
+        }
+    }
+}
+
+// ---- Algorithm 8 (AccuX) in FP64, both roots --------------------------------
+template <bool Renorm>
+__device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (&x2)[3],
+                                           double z0, PairOut &o) {
+    if (!finite7(x1, x2, z0)) return clear(o, 0);
+    // n = x1 x x2 as three compensated pairs
+    double n[3], en[3];
+    accu_dop<double, Renorm>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);  // y1 z2 - z1 y2
+    accu_dop<double, Renorm>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);  // z1 x2 - x1 z2
+    accu_dop<double, Renorm>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);  // x1 y2 - y1 x2
+    double S2, s2, S3, s3;
+    {
+        const double nxy[2] = {n[0], n[1]}, exy[2] = {en[0], en[1]};
+        sum_of_squares_c<double, 2>(nxy, exy, S2, s2);
+        sum_of_squares_c<double, 3>(n, en, S3, s3);
+    }
+    if (S3 == 0.0) return clear(o, -1);
+    if (S2 == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
+    // s^2 = |n_xy|^2 - |n|^2 z0^2 as a pair
+    double C, eC, D, eD, E, eE;
+    two_prod(z0, z0, C, eC);
+    {
+        const double xs[4] = {S3, S3, s3, s3}, ys[4] = {C, eC, C, eC};
+        comp_dot_c<double, 4>(xs, ys, D, eD);
+    }
+    two_sum(S2, -D, E, eE);
+    double e = add(sub(s2, eD), eE);
+    double ss, ess;
+    fast_two_sum(E, e, ss, ess);
+    if (!(ss >= 0.0)) return clear(o, 0);
+    double sb, es;
+    acc_sqrt(ss, ess, sb, es);
+    // F = n_x n_z and n_y n_z with their first-order compensation terms
+    double Fx, eFx, Fy, eFy;
+    two_prod(n[0], n[2], Fx, eFx);
+    eFx = add(add(eFx, mul(n[0], en[2])), mul(n[2], en[0]));
+    two_prod(n[1], n[2], Fy, eFy);
+    eFy = add(add(eFy, mul(n[1], en[2])), mul(n[2], en[1]));
+    // containment vectors from the leading parts of n
+    double m1x = fma_(n[1], x1[2], -mul(n[2], x1[1]));
+    double m1y = fma_(n[2], x1[0], -mul(n[0], x1[2]));
+    double m1z = fma_(n[0], x1[1], -mul(n[1], x1[0]));
+    double m2x = fma_(x2[1], n[2], -mul(x2[2], n[1]));
+    double m2y = fma_(x2[2], n[0], -mul(x2[0], n[2]));
+    double m2z = fma_(x2[0], n[1], -mul(x2[1], n[0]));
+    const int nroots = ss > 0.0 ? 2 : 1;
+    o.count = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o.hit[r] = false;
+        if (r >= nroots) continue;
+        const double sg = r == 0 ? sb : -sb;
+        const double eg = r == 0 ? es : -es;
+        const double xa[6] = {Fx, eFx, n[1], en[1], n[1], en[1]};
+        const double yy[6] = {z0, z0, sg, sg, eg, eg};
+        const double xb[6] = {Fy, eFy, -n[0], -en[0], -n[0], -en[0]};
+        double X = comp_dot<double, 6>(xa, yy);
+        double Y = comp_dot<double, 6>(xb, yy);
+        double Px = -div_(X, S2);
+        double Py = -div_(Y, S2);
+        double t1 = fma_(Px, m1x, fma_(Py, m1y, mul(z0, m1z)));
+        double t2 = fma_(Px, m2x, fma_(Py, m2y, mul(z0, m2z)));
+        o.px[r] = Px;
+        o.py[r] = Py;
+        if (t1 >= 0.0 && t2 >= 0.0) {
+            o.hit[r] = true;
+            ++o.count;
+        }
+    }
+}
+
+// ---- float-float -------------------------------------------------------------
+// Pairs of FP32 (hi + lo, |lo| <= 2^-24 |hi|) carry about 48 bits.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_from(double v) {
+    float h = __double2float_rn(v);
+    float l = __double2float_rn(sub(v, (double)h));
+    return {h, l};
+}
+// v + e (both FP64, |e| << |v|) as float-float
+__device__ __forceinline__ ff ff_from2(double v, double e) {
+    float h = __double2float_rn(v);
+    float l = __double2float_rn(add(sub(v, (double)h), e));
+    return {h, l};
+}
+__device__ __forceinline__ ff ff_norm(float s, float e) {
+    ff r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = add(e, add(a.lo, b.lo));
+    return ff_norm(s, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = fma_(a.hi, b.lo, e);
+    e = fma_(a.lo, b.hi, e);
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+    float p, e;
+    two_prod(a.hi, a.hi, p, e);
+    e = fma_(add(a.hi, a.hi), a.lo, e);
+    return ff_norm(p, e);
+}
+// sqrt of a non-negative float-float (double-word square root, as acc_sqrt)
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+    if (a.hi <= 0.0f) return {0.0f, 0.0f};
+    float r = sqrt_(a.hi);
+    float rem = fma_(-r, r, a.hi);
+    float l = div_(add(rem, a.lo), add(r, r));
+    return ff_norm(r, l);
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return add((double)a.hi, (double)a.lo); }
+
+// binary exponent of |v| for a finite nonzero double (floor(log2 |v|))
+__device__ __forceinline__ int exponent_of(double v) {
+    int hi = __double2hiint(v);
+    int ex = (hi >> 20) & 0x7ff;
+    if (ex == 0) return ilogb(v);  // subnormal
+    return ex - 1023;
+}
+
+__device__ __forceinline__ void pair_ff32(const double (&x1)[3], const double (&x2)[3], double z0,
+                                          PairOut &o) {
+    if (!finite7(x1, x2, z0)) return clear(o, 0);
+    // FP64: the compensated cross product (ill-conditioned for nearly parallel
+    // or antipodal endpoints), renormalised pairs
+    double n[3], en[3];
+    accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
+    accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
+    accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
+    if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return clear(o, -1);
+    if (n[0] == 0.0 && n[1] == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
+    // Eq. 2.2 is homogeneous of degree 0 in n: scale by an exact power of two
+    // so that max |n_i| lies in [1, 2) and FP32 neither underflows nor overflows
+    const double amax = fmax(fabs(n[0]), fmax(fabs(n[1]), fabs(n[2])));
+    const double sc = ldexp(1.0, -exponent_of(amax));
+    double ns[3];
+    ff nf[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ns[i] = mul(n[i], sc);
+        nf[i] = ff_from2(ns[i], mul(en[i], sc));
+    }
+    const ff zf = ff_from(z0);
+    const ff S2 = ff_add(ff_sqr(nf[0]), ff_sqr(nf[1]));
+    const ff S3 = ff_add(S2, ff_sqr(nf[2]));
+    const ff s2 = ff_add(S2, ff_neg(ff_mul(S3, ff_sqr(zf))));
+    if (s2.hi < 0.0f) return clear(o, 0);
+    const ff s = ff_sqrt(s2);
+    const ff Ax = ff_mul(ff_mul(nf[0], nf[2]), zf);  // z0 n_x n_z
+    const ff Ay = ff_mul(ff_mul(nf[1], nf[2]), zf);  // z0 n_y n_z
+    const ff Bx = ff_mul(nf[1], s);                  // s n_y
+    const ff By = ff_mul(nf[0], s);                  // s n_x
+    const double S2d = ff_to_double(S2);
+    // containment in FP64 from the scaled leading parts
+    double m1x = fma_(ns[1], x1[2], -mul(ns[2], x1[1]));
+    double m1y = fma_(ns[2], x1[0], -mul(ns[0], x1[2]));
+    double m1z = fma_(ns[0], x1[1], -mul(ns[1], x1[0]));
+    double m2x = fma_(x2[1], ns[2], -mul(x2[2], ns[1]));
+    double m2y = fma_(x2[2], ns[0], -mul(x2[0], ns[2]));
+    double m2z = fma_(x2[0], ns[1], -mul(x2[1], ns[0]));
+    const int nroots = s2.hi > 0.0f ? 2 : 1;
+    o.count = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o.hit[r] = false;
+        if (r >= nroots) continue;
+        ff X = r == 0 ? ff_add(Ax, Bx) : ff_add(Ax, ff_neg(Bx));
+        ff Y = r == 0 ? ff_add(Ay, ff_neg(By)) : ff_add(Ay, By);
+        double Px = -div_(ff_to_double(X), S2d);
+        double Py = -div_(ff_to_double(Y), S2d);
+        double t1 = fma_(Px, m1x, fma_(Py, m1y, mul(z0, m1z)));
+        double t2 = fma_(Px, m2x, fma_(Py, m2y, mul(z0, m2z)));
+        o.px[r] = Px;
+        o.py[r] = Py;
+        if (t1 >= 0.0 && t2 >= 0.0) {
+            o.hit[r] = true;
+            ++o.count;
+        }
+    }
+}
+
+template <int Mode>
+__device__ __forceinline__ void intersect_pair(const double (&x1)[3], const double (&x2)[3],
+                                               double z0, PairOut &o) {
+    if (Mode == kDirect)
+        pair_direct(x1, x2, z0, o);
+    else if (Mode == kEftFp64)
+        pair_accux<true>(x1, x2, z0, o);
+    else if (Mode == kEftFp64Printed)
+        pair_accux<false>(x1, x2, z0, o);
+    else
+        pair_ff32(x1, x2, z0, o);
+}
+
+}  // namespace sphx

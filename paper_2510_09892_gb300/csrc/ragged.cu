@@ -1,0 +1,408 @@
+// Ragged call: every edge of a mesh batch against every latitude of its mesh
+// in the edge's z-range (steps a11 and a12 of the hot path, around the
+// per-pair evaluation of intersect.cuh).
+//
+//  1. candidate_kernel  per edge: z-range of the arc (endpoint z's, and the
+//                       apex +-|n_xy|/|n| when the arc passes it), widened,
+//                       then two binary searches into the mesh's sorted
+//                       latitudes give [lo, hi).
+//  2. scan_*            exclusive prefix sum of hi - lo over all edges
+//                       (int64): pair p belongs to the edge e with
+//                       offsets[e] <= p < offsets[e + 1].
+//  3. ragged_kernel     persistent grid (a multiple of the SM count); each
+//                       warp claims chunks of 32 * K consecutive pairs from a
+//                       global ticket counter, evaluates them (lane l takes
+//                       pairs l*K .. l*K + K - 1 of the chunk, so record order
+//                       inside a chunk is pair order), counts its hits with a
+//                       warp scan and obtains the chunk's output offset either
+//                       with one atomicAdd (ATOMIC) or by a decoupled
+//                       look-back over the preceding chunks (ORDERED: output in
+//                       pair order, i.e. (edge, lat, root) order).
+#include "common.cuh"
+#include "intersect.cuh"
+
+namespace sphx {
+
+// ---- candidate ranges ---------------------------------------------------------
+// first index i in [0, n) with a[i] > key (n if none)
+template <typename T>
+__device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t n, T key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] > key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+// first index i in [0, n) with a[i] >= key
+__device__ __forceinline__ int64_t lower_bound_dev(const double *a, int64_t n, double key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] >= key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+constexpr double kZWiden = 1e-13;
+
+__global__ void candidate_kernel(const double *__restrict__ A, const double *__restrict__ B,
+                                 const int64_t *__restrict__ edge_offsets, int M, int64_t E,
+                                 const double *__restrict__ lat_z, int64_t L,
+                                 const int64_t *__restrict__ lat_offsets,
+                                 int32_t *__restrict__ lo_out, int32_t *__restrict__ hi_out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        // the offsets live on the device and are not validated by the host:
+        // clamp every index derived from them into its buffer
+        int m = (int)upper_bound_dev<int64_t>(edge_offsets, M + 1, e) - 1;
+        m = m < 0 ? 0 : (m >= M ? M - 1 : m);
+        int64_t ls = lat_offsets[m], le = lat_offsets[m + 1];
+        ls = ls < 0 ? 0 : (ls > L ? L : ls);
+        le = le < ls ? ls : (le > L ? L : le);
+        const double x1[3] = {A[3 * e], A[3 * e + 1], A[3 * e + 2]};
+        const double x2[3] = {B[3 * e], B[3 * e + 1], B[3 * e + 2]};
+        int32_t lo = (int32_t)ls, hi = (int32_t)ls;
+        double n[3], en[3];
+        accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
+        accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
+        accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
+        const bool ok = finite7(x1, x2, 0.0) && (n[0] != 0.0 || n[1] != 0.0 || n[2] != 0.0);
+        if (ok) {
+            const double z1 = x1[2] * rsqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
+            const double z2 = x2[2] * rsqrt(x2[0] * x2[0] + x2[1] * x2[1] + x2[2] * x2[2]);
+            double zmin = fmin(z1, z2), zmax = fmax(z1, z2);
+            // scale n to avoid underflow in the squares of very short arcs
+            const double amax = fmax(fabs(n[0]), fmax(fabs(n[1]), fabs(n[2])));
+            const double sc = ldexp(1.0, -exponent_of(amax));
+            const double nx = n[0] * sc, ny = n[1] * sc, nz = n[2] * sc;
+            const double S2 = nx * nx + ny * ny, S3 = S2 + nz * nz;
+            // highest point of the great circle: a = (-nx nz, -ny nz, S2); it is on
+            // the arc iff a . (n x x1) >= 0 and a . (x2 x n) >= 0 (the lowest is -a)
+            const double ax = -nx * nz, ay = -ny * nz, az = S2;
+            const double m1x = ny * x1[2] - nz * x1[1], m1y = nz * x1[0] - nx * x1[2],
+                         m1z = nx * x1[1] - ny * x1[0];
+            const double m2x = x2[1] * nz - x2[2] * ny, m2y = x2[2] * nx - x2[0] * nz,
+                         m2z = x2[0] * ny - x2[1] * nx;
+            const double t1 = ax * m1x + ay * m1y + az * m1z;
+            const double t2 = ax * m2x + ay * m2y + az * m2z;
+            const double zap = sqrt(S2 / S3);
+            if (t1 >= 0.0 && t2 >= 0.0) zmax = zap;
+            if (t1 <= 0.0 && t2 <= 0.0) zmin = -zap;
+            zmin -= kZWiden;
+            zmax += kZWiden;
+            const double *lz = lat_z + ls;
+            lo = (int32_t)(ls + lower_bound_dev(lz, le - ls, zmin));
+            hi = (int32_t)(ls + upper_bound_dev<double>(lz, le - ls, zmax));
+            if (hi < lo) hi = lo;
+        }
+        lo_out[e] = lo;
+        hi_out[e] = hi;
+    }
+}
+
+// ---- exclusive scan of (hi - lo) into int64 offsets[E + 1] ----------------------
+constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long count_of(const int32_t *lo, const int32_t *hi, int64_t e) {
+    const int d = hi[e] - lo[e];
+    return d > 0 ? d : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *warp_sums, T &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    total = warp_sums[nw - 1];
+    T before = warp > 0 ? warp_sums[warp - 1] : T(0);
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_reduce(const int32_t *__restrict__ lo, const int32_t *__restrict__ hi, int64_t E,
+                long long *__restrict__ block_sums) {
+    __shared__ long long ws[32];
+    const int64_t base = blockIdx.x * (int64_t)kScanTile;
+    long long s = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+        const int64_t e = base + i;
+        if (e < E) s += count_of(lo, hi, e);
+    }
+    long long total;
+    block_exclusive_scan<long long>(s, ws, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// one block: exclusive scan of block_sums[0..nb) in place; total -> block_sums[nb], *tail
+__global__ void __launch_bounds__(1024)
+    scan_blocks(long long *__restrict__ block_sums, int64_t nb, long long *__restrict__ tail) {
+    __shared__ long long ws[32];
+    long long carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int64_t b = b0 + threadIdx.x;
+        long long v = b < nb ? block_sums[b] : 0;
+        long long total;
+        long long ex = block_exclusive_scan<long long>(v, ws, total);
+        if (b < nb) block_sums[b] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        block_sums[nb] = carry;
+        *tail = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_apply(const int32_t *__restrict__ lo, const int32_t *__restrict__ hi, int64_t E,
+               const long long *__restrict__ block_sums, long long *__restrict__ offsets) {
+    __shared__ long long ws[32];
+    const int64_t base = blockIdx.x * (int64_t)kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long c[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        c[i] = e < E ? count_of(lo, hi, e) : 0;
+        s += c[i];
+    }
+    long long total;
+    long long ex = block_exclusive_scan<long long>(s, ws, total) + block_sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (e < E) offsets[e] = ex;
+        ex += c[i];
+    }
+}
+
+// ---- persistent intersection + compaction ----------------------------------------
+// look-back word: flag (2 bits) | tag (22 bits) | value (40 bits)
+constexpr unsigned long long kFlagAgg = 1ull, kFlagInc = 2ull;
+__device__ __forceinline__ unsigned long long lb_pack(unsigned long long flag,
+                                                      unsigned long long tag,
+                                                      unsigned long long v) {
+    return (flag << 62) | ((tag & 0x3fffffull) << 40) | (v & 0xffffffffffull);
+}
+
+
+
+template <int Mode, int K, bool Ordered>
+__global__ void ragged_kernel(RaggedArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long T = a.offsets[a.E];
+    constexpr int CH = 32 * K;
+    const long long nchunks = (T + CH - 1) / CH;
+    const int ring_bits = __ffsll(a.ring_slots) - 1;
+    while (true) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(a.counters, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if ((long long)c >= nchunks) break;
+        const long long p0 = (long long)c * CH;
+        const long long p1 = min(p0 + CH, T);
+        // edges of the first and last pair of the chunk
+        long long ef = 0;
+        if (lane < 2) {
+            const long long key = lane == 0 ? p0 : p1 - 1;
+            ef = upper_bound_dev<long long>(a.offsets, a.E + 1, key) - 1;
+        }
+        const long long e_first = __shfl_sync(0xffffffffu, ef, 0);
+        const long long e_last = __shfl_sync(0xffffffffu, ef, 1);
+        PairOut res[K];
+        long long edge[K];
+        int32_t lat[K];
+        int h = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const long long p = p0 + (long long)lane * K + j;
+            res[j].count = 0;
+            res[j].hit[0] = res[j].hit[1] = false;
+            edge[j] = 0;
+            lat[j] = 0;
+            if (p < p1) {
+                const long long e =
+                    e_first + upper_bound_dev<long long>(a.offsets + e_first, e_last - e_first + 1, p) - 1;
+                const long long k = a.lo[e] + (p - a.offsets[e]);
+                edge[j] = e;
+                lat[j] = (int32_t)k;
+                if (k < 0 || k >= a.L) {
+                    atomicOr(a.status, kStatusScratch);
+                    continue;
+                }
+                const double x1[3] = {a.A[3 * e], a.A[3 * e + 1], a.A[3 * e + 2]};
+                const double x2[3] = {a.B[3 * e], a.B[3 * e + 1], a.B[3 * e + 2]};
+                intersect_pair<Mode>(x1, x2, a.lat_z[k], res[j]);
+                h += (int)res[j].hit[0] + (int)res[j].hit[1];
+            }
+        }
+        // warp scan of the hit counts
+        int incl = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned long long total = (unsigned)__shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0) {
+            if (!Ordered) {
+                base = total ? atomicAdd(a.out_total, total) : 0ull;
+            } else {
+                const unsigned long long mask = (unsigned long long)a.ring_slots - 1;
+                const unsigned long long tag = c >> ring_bits;
+                if (c == 0) {
+                    atomicExch(a.ring, lb_pack(kFlagInc, 0, total));
+                } else {
+                    atomicExch(a.ring + (c & mask), lb_pack(kFlagAgg, tag, total));
+                    unsigned long long run = 0;
+                    long long j = (long long)c - 1;
+                    long long spins = 0;
+                    while (j >= 0) {
+                        const unsigned long long w =
+                            *reinterpret_cast<volatile unsigned long long *>(a.ring + (j & mask));
+                        const unsigned long long f = w >> 62;
+                        const unsigned long long wt = (w >> 40) & 0x3fffffull;
+                        if (f != 0 && wt == (((unsigned long long)j >> ring_bits) & 0x3fffffull)) {
+                            run += w & 0xffffffffffull;
+                            if (f == kFlagInc) break;
+                            --j;
+                            continue;
+                        }
+                        if (++spins > kSpinLimit) {
+                            atomicOr(a.status, kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                    base = run;
+                    atomicExch(a.ring + (c & mask), lb_pack(kFlagInc, tag, run + total));
+                }
+                if ((long long)c == nchunks - 1) *a.out_total = base + total;
+            }
+            if (base + total > (unsigned long long)a.cap) atomicOr(a.status, kStatusCapacity);
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        unsigned long long idx = base + (unsigned long long)(incl - h);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (res[j].hit[r]) {
+                    if (idx < (unsigned long long)a.cap) {
+                        sphx_hit rec;
+                        rec.edge = edge[j];
+                        rec.lat = lat[j];
+                        rec.root = r;
+                        rec.x = res[j].px[r];
+                        rec.y = res[j].py[r];
+                        a.out[idx] = rec;
+                    }
+                    ++idx;
+                }
+            }
+        }
+    }
+}
+
+// ---- host side -----------------------------------------------------------------
+typedef void (*RaggedKernelFn)(RaggedArgs);
+
+template <int Mode>
+static RaggedKernelFn pick_k(int K, bool ordered) {
+    if (ordered) {
+        if (K == 1) return ragged_kernel<Mode, 1, true>;
+        if (K == 2) return ragged_kernel<Mode, 2, true>;
+        return ragged_kernel<Mode, 4, true>;
+    }
+    if (K == 1) return ragged_kernel<Mode, 1, false>;
+    if (K == 2) return ragged_kernel<Mode, 2, false>;
+    return ragged_kernel<Mode, 4, false>;
+}
+
+static RaggedKernelFn pick_kernel(int mode, int K, bool ordered) {
+    switch (mode) {
+        case kDirect: return pick_k<kDirect>(K, ordered);
+        case kEftFp64: return pick_k<kEftFp64>(K, ordered);
+        case kEftFf32: return pick_k<kEftFf32>(K, ordered);
+        default: return pick_k<kEftFp64Printed>(K, ordered);
+    }
+}
+
+int64_t scan_blocks_for(int64_t E) { return (E + kScanTile - 1) / kScanTile; }
+
+cudaError_t launch_candidates(const double *A, const double *B, const int64_t *edge_offsets,
+                              int M, int64_t E, const double *lat_z, int64_t L,
+                              const int64_t *lat_offsets, int32_t *lo, int32_t *hi,
+                              int sm_count, cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((E + 255) / 256, (int64_t)sm_count * 16);
+    candidate_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, B, edge_offsets, M, E, lat_z, L,
+                                                      lat_offsets, lo, hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int32_t *lo, const int32_t *hi, int64_t E, long long *block_sums,
+                        long long *offsets, cudaStream_t s) {
+    const int64_t nb = scan_blocks_for(E);
+    scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(lo, hi, E, block_sums);
+    scan_blocks<<<1, 1024, 0, s>>>(block_sums, nb, offsets + E);
+    scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(lo, hi, E, block_sums, offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, int sm_count,
+                          cudaStream_t s) {
+    RaggedKernelFn fn = pick_kernel(mode, sh.pairs_per_lane, sh.compaction == SPHX_COMPACT_ORDERED);
+    const unsigned grid = (unsigned)(sm_count * sh.blocks_per_sm);
+    fn<<<grid, sh.threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sphx
+
+using namespace sphx;
+
+extern "C" sphx_status sphx_candidate_ranges(const double *A, const double *B,
+                                             const int64_t *edge_offsets, int32_t M, int64_t E,
+                                             const double *lat_z, const int64_t *lat_offsets,
+                                             int64_t L, int32_t *lo, int32_t *hi,
+                                             sphx_stream stream) {
+    if (M < 1 || E < 0 || L < 0 || L > INT32_MAX) return SPHX_ERR_INVALID_ARG;
+    if (E == 0) return SPHX_OK;
+    if (!A || !B || !edge_offsets || !lat_z || !lat_offsets || !lo || !hi)
+        return SPHX_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_candidates(A, B, edge_offsets, M, E, lat_z, L, lat_offsets, lo, hi,
+                                      sms > 0 ? sms : 1, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return SPHX_ERR_CUDA;
+    }
+    return SPHX_OK;
+}

@@ -1,0 +1,487 @@
+// Host runtime of the C ABI: contexts, the device status word, scratch of the
+// ragged call, its CUDA-graph cache and autotuner, and the FMA peak probe.
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace sphx {
+
+static char g_cuda_error[256] = "";
+
+void set_cuda_error(cudaError_t e) {
+    std::snprintf(g_cuda_error, sizeof g_cuda_error, "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+}
+
+}  // namespace sphx
+
+using namespace sphx;
+
+namespace {
+
+constexpr int64_t kMaxRingSlots = int64_t(1) << 21;
+
+int64_t ring_slots_for(const sphx_context *ctx, const RaggedShape &sh) {
+    // the look-back never reads further back than the warps in flight; 16x
+    // headroom keeps a slot from being reused while a slow warp still reads it
+    const int64_t warps = (int64_t)ctx->sm_count * sh.blocks_per_sm * (sh.threads / 32);
+    int64_t r = 65536;
+    while (r < 16 * warps && r < kMaxRingSlots) r <<= 1;
+    return r;
+}
+
+void free_scratch(RaggedScratch &s) {
+    cudaFree(s.lo);
+    cudaFree(s.hi);
+    cudaFree(s.offsets);
+    cudaFree(s.block_sums);
+    cudaFree(s.ring);
+    cudaFree(s.counters);
+    s = RaggedScratch();
+}
+
+void drop_graphs(sphx_context *ctx) {
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+sphx_status ensure_scratch(sphx_context *ctx, int64_t E) {
+    RaggedScratch &s = ctx->scratch;
+    if (s.E >= E && s.ring) return SPHX_OK;
+    // growing: nothing may still use the old buffers
+    SPHX_CUDA(cudaDeviceSynchronize());
+    drop_graphs(ctx);
+    free_scratch(s);
+    const int64_t cap = E + E / 4 + 1024;  // headroom so slightly larger batches reuse it
+    const int64_t nb = scan_blocks_for(cap);
+    if (std::getenv("SPHX_FAULT") && std::strcmp(std::getenv("SPHX_FAULT"), "alloc") == 0)
+        return SPHX_ERR_NOMEM;
+    bool ok = cudaMalloc(&s.lo, cap * sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc(&s.hi, cap * sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc(&s.offsets, (cap + 1) * sizeof(long long)) == cudaSuccess &&
+              cudaMalloc(&s.block_sums, (nb + 1) * sizeof(long long)) == cudaSuccess &&
+              cudaMalloc(&s.ring, kMaxRingSlots * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&s.counters, 4 * sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_scratch(s);
+        return SPHX_ERR_NOMEM;
+    }
+    s.E = cap;
+    s.nb = nb;
+    s.ring_slots = kMaxRingSlots;
+    return SPHX_OK;
+}
+
+struct RaggedCall {
+    const double *A, *B;
+    const int64_t *edge_offsets;
+    int32_t M;
+    int64_t E;
+    const double *lat_z;
+    const int64_t *lat_offsets;
+    int64_t L;
+    const int32_t *lo, *hi;
+    int mode;
+    sphx_hit *out;
+    int64_t cap;
+    int64_t *out_total;
+};
+
+// enqueue the whole ragged sequence on stream s (capturable)
+cudaError_t enqueue_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedShape &sh,
+                           cudaStream_t s) {
+    RaggedScratch &sc = ctx->scratch;
+    const int32_t *lo = c.lo, *hi = c.hi;
+    cudaError_t e;
+    if (!lo) {
+        e = launch_candidates(c.A, c.B, c.edge_offsets, c.M, c.E, c.lat_z, c.L, c.lat_offsets, sc.lo,
+                              sc.hi, ctx->sm_count, s);
+        if (e != cudaSuccess) return e;
+        lo = sc.lo;
+        hi = sc.hi;
+    }
+    if ((e = launch_scan(lo, hi, c.E, sc.block_sums, sc.offsets, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(c.out_total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+    const int64_t slots = ring_slots_for(ctx, sh);
+    if (sh.compaction == SPHX_COMPACT_ORDERED &&
+        (e = cudaMemsetAsync(sc.ring, 0, slots * sizeof(unsigned long long), s)) != cudaSuccess)
+        return e;
+    RaggedArgs a;
+    a.A = c.A;
+    a.B = c.B;
+    a.lat_z = c.lat_z;
+    a.lo = lo;
+    a.offsets = sc.offsets;
+    a.E = c.E;
+    a.L = c.L;
+    a.out = c.out;
+    a.cap = c.cap;
+    a.out_total = reinterpret_cast<unsigned long long *>(c.out_total);
+    a.counters = sc.counters;
+    a.ring = sc.ring;
+    a.ring_slots = slots;
+    a.status = ctx->status;
+    return launch_ragged(c.mode, sh, a, ctx->sm_count, s);
+}
+
+sphx_status check_ragged_args(const RaggedCall &c) {
+    if (c.M < 1 || c.E < 0 || c.L < 0 || c.L > INT32_MAX || c.cap < 0) return SPHX_ERR_INVALID_ARG;
+    if (c.mode < 0 || c.mode > 3) return SPHX_ERR_INVALID_ARG;
+    if (!c.out_total || (c.cap > 0 && !c.out)) return SPHX_ERR_INVALID_ARG;
+    if ((c.lo == nullptr) != (c.hi == nullptr)) return SPHX_ERR_INVALID_ARG;
+    if (c.E > 0 && (!c.A || !c.B || !c.edge_offsets || !c.lat_z || !c.lat_offsets))
+        return SPHX_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(c.out) & 15u) || (reinterpret_cast<uintptr_t>(c.out_total) & 7u))
+        return SPHX_ERR_INVALID_ARG;
+    return SPHX_OK;
+}
+
+RaggedShape effective_shape(const sphx_context *ctx) {
+    RaggedShape sh = ctx->shape;
+    if (sh.compaction == SPHX_COMPACT_AUTO) sh.compaction = SPHX_COMPACT_ATOMIC;
+    return sh;
+}
+
+sphx_status run_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedShape &sh,
+                       cudaStream_t s) {
+    if (c.E == 0) {
+        SPHX_CUDA(cudaMemsetAsync(c.out_total, 0, sizeof(int64_t), s));
+        return SPHX_OK;
+    }
+    sphx_status st = ensure_scratch(ctx, c.E);
+    if (st != SPHX_OK) return st;
+    if (!sh.use_graph) {
+        SPHX_CUDA(enqueue_ragged(ctx, c, sh, s));
+        return SPHX_OK;
+    }
+    GraphKey key;
+    key.v = {(uintptr_t)c.A, (uintptr_t)c.B, (uintptr_t)c.edge_offsets, (uintptr_t)c.M,
+             (uintptr_t)c.E, (uintptr_t)c.lat_z, (uintptr_t)c.lat_offsets, (uintptr_t)c.L,
+             (uintptr_t)c.lo, (uintptr_t)c.hi, (uintptr_t)c.mode, (uintptr_t)c.out,
+             (uintptr_t)c.cap, (uintptr_t)c.out_total, (uintptr_t)sh.threads,
+             (uintptr_t)sh.blocks_per_sm, (uintptr_t)sh.pairs_per_lane,
+             (uintptr_t)sh.compaction};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 64) drop_graphs(ctx);
+        cudaGraph_t g = nullptr;
+        SPHX_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_ragged(ctx, c, sh, ctx->capture_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_cuda_error(e != cudaSuccess ? e : e2);
+            cudaGetLastError();
+            return SPHX_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        SPHX_CUDA(e);
+        it = ctx->graphs.emplace(key, ex).first;
+    }
+    SPHX_CUDA(cudaGraphLaunch(it->second, s));
+    return SPHX_OK;
+}
+
+template <typename T>
+__global__ void fma_probe(T *out, int iters, T a, T b) {
+    T x0 = T(threadIdx.x) * T(1e-3), x1 = x0 + T(1), x2 = x0 + T(2), x3 = x0 + T(3);
+    T x4 = x0 + T(4), x5 = x0 + T(5), x6 = x0 + T(6), x7 = x0 + T(7);
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b);
+        x1 = fma(x1, a, b);
+        x2 = fma(x2, a, b);
+        x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b);
+        x5 = fma(x5, a, b);
+        x6 = fma(x6, a, b);
+        x7 = fma(x7, a, b);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+// 32-bit integer multiply-add chains (IMAD), the same shape as fma_probe
+__global__ void imad_probe(unsigned *out, int iters, unsigned a, unsigned b) {
+    unsigned x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+    unsigned x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = x0 * a + b;
+        x1 = x1 * a + b;
+        x2 = x2 * a + b;
+        x3 = x3 * a + b;
+        x4 = x4 * a + b;
+        x5 = x5 * a + b;
+        x6 = x6 * a + b;
+        x7 = x7 * a + b;
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = ((x0 ^ x1) ^ (x2 ^ x3)) ^ ((x4 ^ x5) ^ (x6 ^ x7));
+}
+
+sphx_status probe_imad(double *ops) {
+    int dev = 0, sms = 0;
+    SPHX_CUDA(cudaGetDevice(&dev));
+    SPHX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = sms * 8, iters = 16384;
+    unsigned *out = nullptr;
+    SPHX_CUDA(cudaMalloc(&out, sizeof(unsigned) * threads * blocks));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0);
+        imad_probe<<<blocks, threads>>>(out, iters, 1664525u, 1013904223u);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    SPHX_CUDA(e);
+    *ops = 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+    return SPHX_OK;
+}
+
+template <typename T>
+sphx_status probe(double *flops) {
+    int dev = 0, sms = 0;
+    SPHX_CUDA(cudaGetDevice(&dev));
+    SPHX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, blocks = sms * 8;
+    const int iters = sizeof(T) == 8 ? 4096 : 65536;
+    T *out = nullptr;
+    SPHX_CUDA(cudaMalloc(&out, sizeof(T) * threads * blocks));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0);
+        fma_probe<T><<<blocks, threads>>>(out, iters, T(0.999999), T(1e-6));
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    SPHX_CUDA(e);
+    *flops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+    return SPHX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sphx_status sphx_create(sphx_context **out, int device) {
+    if (!out) return SPHX_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    SPHX_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return SPHX_ERR_INVALID_ARG;
+    SPHX_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    SPHX_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (!(prop.major == 10 && prop.minor == 3)) return SPHX_ERR_UNSUPPORTED;
+    sphx_context *ctx = new sphx_context();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    if (cudaMalloc(&ctx->status, 256) != cudaSuccess) {
+        delete ctx;
+        return SPHX_ERR_NOMEM;
+    }
+    cudaMemset(ctx->status, 0, 256);
+    if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(ctx->status);
+        delete ctx;
+        return SPHX_ERR_CUDA;
+    }
+    cudaDeviceSynchronize();
+    *out = ctx;
+    return SPHX_OK;
+}
+
+void sphx_destroy(sphx_context *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    free_scratch(ctx->scratch);
+    cudaFree(ctx->status);
+    cudaStreamDestroy(ctx->capture_stream);
+    delete ctx;
+}
+
+sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const double *B,
+                                  const int64_t *edge_offsets, int32_t M, int64_t E,
+                                  const double *lat_z, const int64_t *lat_offsets, int64_t L,
+                                  const int32_t *edge_lat_lo, const int32_t *edge_lat_hi,
+                                  sphx_mode mode, sphx_hit *out, int64_t out_cap,
+                                  int64_t *out_total, sphx_stream stream) {
+    if (!ctx) return SPHX_ERR_INVALID_ARG;
+    RaggedCall c{A, B, edge_offsets, M, E, lat_z, lat_offsets, L, edge_lat_lo, edge_lat_hi,
+                 (int)mode, out, out_cap, out_total};
+    sphx_status st = check_ragged_args(c);
+    if (st != SPHX_OK) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return run_ragged(ctx, c, effective_shape(ctx), reinterpret_cast<cudaStream_t>(stream));
+}
+
+sphx_status sphx_sync_status(sphx_context *ctx, sphx_stream stream) {
+    if (!ctx) return SPHX_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPHX_CUDA(cudaStreamSynchronize(s));
+    unsigned h = 0;
+    SPHX_CUDA(cudaMemcpy(&h, ctx->status, sizeof h, cudaMemcpyDeviceToHost));
+    SPHX_CUDA(cudaMemset(ctx->status, 0, sizeof h));
+    if (h & kStatusTimeout) return SPHX_ERR_TIMEOUT;
+    if (h & kStatusScratch) return SPHX_ERR_INVALID_ARG;
+    if (h & kStatusCapacity) return SPHX_ERR_CAPACITY;
+    return SPHX_OK;
+}
+
+sphx_status sphx_set_tuning(sphx_context *ctx, const sphx_tuning *t) {
+    if (!ctx) return SPHX_ERR_INVALID_ARG;
+    if (!t) {
+        ctx->shape = RaggedShape();
+        ctx->tuned = false;
+        return SPHX_OK;
+    }
+    RaggedShape sh = ctx->shape;
+    if (t->threads_per_block) {
+        if (t->threads_per_block < 64 || t->threads_per_block > 1024 || t->threads_per_block % 32)
+            return SPHX_ERR_INVALID_ARG;
+        sh.threads = t->threads_per_block;
+    }
+    if (t->blocks_per_sm) {
+        if (t->blocks_per_sm < 1 || t->blocks_per_sm > 16) return SPHX_ERR_INVALID_ARG;
+        sh.blocks_per_sm = t->blocks_per_sm;
+    }
+    if (t->pairs_per_lane) {
+        if (t->pairs_per_lane != 1 && t->pairs_per_lane != 2 && t->pairs_per_lane != 4)
+            return SPHX_ERR_INVALID_ARG;
+        sh.pairs_per_lane = t->pairs_per_lane;
+    }
+    if (t->compaction < 0 || t->compaction > 2) return SPHX_ERR_INVALID_ARG;
+    sh.compaction = t->compaction;
+    sh.use_graph = t->use_graph ? 1 : 0;
+    if ((int64_t)ctx->sm_count * sh.blocks_per_sm * sh.threads > (int64_t)ctx->sm_count * 2048)
+        return SPHX_ERR_INVALID_ARG;  // more threads than an SM holds
+    ctx->shape = sh;
+    ctx->tuned = true;
+    return SPHX_OK;
+}
+
+sphx_status sphx_get_tuning(sphx_context *ctx, sphx_tuning *t) {
+    if (!ctx || !t) return SPHX_ERR_INVALID_ARG;
+    const RaggedShape sh = ctx->shape;
+    t->threads_per_block = sh.threads;
+    t->blocks_per_sm = sh.blocks_per_sm;
+    t->pairs_per_lane = sh.pairs_per_lane;
+    t->compaction = sh.compaction;
+    t->use_graph = sh.use_graph;
+    return SPHX_OK;
+}
+
+sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const double *B,
+                                 const int64_t *edge_offsets, int32_t M, int64_t E,
+                                 const double *lat_z, const int64_t *lat_offsets, int64_t L,
+                                 sphx_mode mode, sphx_hit *out, int64_t out_cap,
+                                 int64_t *out_total, sphx_stream stream, double *ms_out) {
+    if (!ctx) return SPHX_ERR_INVALID_ARG;
+    RaggedCall c{A, B, edge_offsets, M, E, lat_z, lat_offsets, L, nullptr, nullptr,
+                 (int)mode, out, out_cap, out_total};
+    sphx_status st = check_ragged_args(c);
+    if (st != SPHX_OK) return st;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (E == 0) return SPHX_OK;
+    if ((st = ensure_scratch(ctx, E)) != SPHX_OK) return st;
+    const int requested = ctx->shape.compaction;
+    std::vector<int> comps;
+    if (requested == SPHX_COMPACT_AUTO)
+        comps = {SPHX_COMPACT_ATOMIC, SPHX_COMPACT_ORDERED};
+    else
+        comps = {requested};
+    cudaEvent_t e0, e1;
+    SPHX_CUDA(cudaEventCreate(&e0));
+    SPHX_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    RaggedShape best_sh = effective_shape(ctx);
+    for (int comp : comps)
+        for (int threads : {128, 256})
+            for (int bps : {2, 4, 8})
+                for (int K : {1, 2, 4}) {
+                    if (threads * bps > 2048) continue;
+                    RaggedShape sh;
+                    sh.threads = threads;
+                    sh.blocks_per_sm = bps;
+                    sh.pairs_per_lane = K;
+                    sh.compaction = comp;
+                    sh.use_graph = 0;
+                    SPHX_CUDA(enqueue_ragged(ctx, c, sh, s));  // warm-up
+                    float tot = 0;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        SPHX_CUDA(cudaEventRecord(e0, s));
+                        SPHX_CUDA(enqueue_ragged(ctx, c, sh, s));
+                        SPHX_CUDA(cudaEventRecord(e1, s));
+                        SPHX_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tot += ms;
+                    }
+                    if (tot / 3 < best) {
+                        best = tot / 3;
+                        best_sh = sh;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the trial runs may have set status bits (e.g. a capacity overflow when
+    // the caller's buffer is only sized for timing): they are not the
+    // caller's, so clear them once the trials are done
+    SPHX_CUDA(cudaStreamSynchronize(s));
+    SPHX_CUDA(cudaMemset(ctx->status, 0, sizeof(unsigned)));
+    best_sh.use_graph = 1;
+    if (requested != SPHX_COMPACT_AUTO) best_sh.compaction = requested;
+    ctx->shape = best_sh;
+    ctx->tuned = true;
+    if (ms_out) *ms_out = best;
+    return SPHX_OK;
+}
+
+sphx_status sphx_probe_fma_rate(int pipe, double *rate) {
+    if (!rate || pipe < 0 || pipe > 2) return SPHX_ERR_INVALID_ARG;
+    if (pipe == 2) return probe_imad(rate);
+    return pipe == 1 ? probe<double>(rate) : probe<float>(rate);
+}
+
+const char *sphx_status_string(sphx_status s) {
+    switch (s) {
+        case SPHX_OK: return "ok";
+        case SPHX_ERR_INVALID_ARG: return "invalid argument";
+        case SPHX_ERR_CUDA: return "CUDA error";
+        case SPHX_ERR_CAPACITY: return "output capacity exceeded";
+        case SPHX_ERR_TIMEOUT: return "device wait timed out";
+        case SPHX_ERR_NOMEM: return "out of device memory";
+        case SPHX_ERR_UNSUPPORTED: return "unsupported device or feature";
+    }
+    return "unknown status";
+}
+
+const char *sphx_last_cuda_error(void) { return g_cuda_error; }
+
+}  // extern "C"

@@ -1,0 +1,275 @@
+"""Python binding of libsphx.so (include/sphx.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name. Tensors are
+passed as raw device pointers; PyTorch only provides device memory and
+streams. There is no CPU path: if the CUDA library cannot be loaded, the
+import of this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsphx.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sphx.h")
+
+# sphx_status
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = range(7)
+# sphx_mode
+MODE_DIRECT_FP64, MODE_EFT_FP64, MODE_EFT_FF32, MODE_EFT_FP64_PRINTED = range(4)
+MODES = {"direct": MODE_DIRECT_FP64, "eft": MODE_EFT_FP64, "ff32": MODE_EFT_FF32,
+         "eft_printed": MODE_EFT_FP64_PRINTED}
+# sphx_compaction
+COMPACT_AUTO, COMPACT_ATOMIC, COMPACT_ORDERED = range(3)
+
+HIT_DTYPE = [("edge", "<i8"), ("lat", "<i4"), ("root", "<i4"), ("x", "<f8"), ("y", "<f8")]
+HIT_BYTES = 32
+
+
+class SphxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = f"{what}: {status_string(status)}"
+        if status == ERR_CUDA:
+            msg += f" ({last_cuda_error()})"
+        super().__init__(msg)
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("pairs_per_lane", ctypes.c_int32), ("compaction", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+_SIGS = {
+    "sphx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
+    "sphx_destroy": (None, [_vp]),
+    "sphx_intersect_gca_constlat": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
+    "sphx_candidate_ranges": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "sphx_intersect_ragged": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp,
+                                             ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "sphx_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "sphx_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
+    "sphx_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
+    "sphx_autotune_ragged": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64,
+                                            ctypes.c_int, _vp, _i64, _vp, _vp,
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "sphx_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sphx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sphx_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions include/sphx.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sphx_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """The loaded libsphx.so, built in-tree first if needed (never a fallback)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        if not os.path.exists(LIB_PATH) or not _build.up_to_date():
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().sphx_status_string(status).decode()
+
+
+def last_cuda_error() -> str:
+    return lib().sphx_last_cuda_error().decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise SphxError(status, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"expected a torch.Tensor or a device pointer, got {type(t)}")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _mode(mode) -> int:
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def _dev_tensor(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+# ------------------------------------------------------------------ dense --
+def sphx_intersect_gca_constlat(A, B, z0, out_pts, out_count, mode="eft", stream=None):
+    """Dense call: arc (A[i], B[i]) against latitude z0[i] (see include/sphx.h).
+
+    A, B: (n, 3) float64 CUDA tensors; z0: (n,) float64; out_pts: (n, 2, 3)
+    float64; out_count: (n,) int32. Stream-ordered, returns after enqueue.
+    """
+    n = int(z0.shape[0])
+    _dev_tensor(A, torch.float64, "A", (n, 3))
+    _dev_tensor(B, torch.float64, "B", (n, 3))
+    _dev_tensor(z0, torch.float64, "z0", (n,))
+    _dev_tensor(out_pts, torch.float64, "out_pts", (n, 2, 3))
+    _dev_tensor(out_count, torch.int32, "out_count", (n,))
+    st = lib().sphx_intersect_gca_constlat(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_pts),
+                                           _ptr(out_count), _mode(mode), _stream(stream))
+    _check(st, "sphx_intersect_gca_constlat")
+
+
+def intersect(A, B, z0, mode="eft", stream=None):
+    """Allocate outputs and run the dense call; returns (out_pts, out_count)."""
+    n = int(z0.shape[0])
+    pts = torch.empty((n, 2, 3), dtype=torch.float64, device=z0.device)
+    cnt = torch.empty((n,), dtype=torch.int32, device=z0.device)
+    sphx_intersect_gca_constlat(A, B, z0, pts, cnt, mode, stream)
+    return pts, cnt
+
+
+# ----------------------------------------------------------------- ragged --
+class Context:
+    """Owns an sphx_context (scratch, status word, tuning, graphs) on one device."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(lib().sphx_create(ctypes.byref(h), int(device)), "sphx_create")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            lib().sphx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tuning(self, threads_per_block=0, blocks_per_sm=0, pairs_per_lane=0,
+                   compaction=COMPACT_AUTO, use_graph=1):
+        t = Tuning(threads_per_block, blocks_per_sm, pairs_per_lane, compaction, use_graph)
+        _check(lib().sphx_set_tuning(self.handle, ctypes.byref(t)), "sphx_set_tuning")
+
+    def reset_tuning(self):
+        _check(lib().sphx_set_tuning(self.handle, None), "sphx_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().sphx_get_tuning(self.handle, ctypes.byref(t)), "sphx_get_tuning")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def sync_status(self, stream=None) -> int:
+        return lib().sphx_sync_status(self.handle, _stream(stream))
+
+
+def sphx_candidate_ranges(A, B, edge_offsets, lat_z, lat_offsets, lo, hi, stream=None):
+    """Per-edge candidate latitude ranges [lo, hi) (global latitude indices)."""
+    M = int(edge_offsets.shape[0]) - 1
+    E = int(A.shape[0])
+    L = int(lat_z.shape[0])
+    _check(lib().sphx_candidate_ranges(_ptr(A), _ptr(B), _ptr(edge_offsets), M, E, _ptr(lat_z),
+                                       _ptr(lat_offsets), L, _ptr(lo), _ptr(hi), _stream(stream)),
+           "sphx_candidate_ranges")
+
+
+def sphx_intersect_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, out, out_total,
+                          mode="eft", edge_lat_lo=None, edge_lat_hi=None, stream=None):
+    """Ragged call (see include/sphx.h). out: uint8/int8 CUDA tensor of cap*32 bytes
+    (or any contiguous tensor whose byte size is a multiple of 32); out_total: (1,) int64."""
+    M = int(edge_offsets.shape[0]) - 1
+    E = int(A.shape[0])
+    L = int(lat_z.shape[0])
+    _dev_tensor(A, torch.float64, "A", (E, 3))
+    _dev_tensor(B, torch.float64, "B", (E, 3))
+    _dev_tensor(edge_offsets, torch.int64, "edge_offsets")
+    _dev_tensor(lat_offsets, torch.int64, "lat_offsets", (M + 1,))
+    _dev_tensor(out_total, torch.int64, "out_total", (1,))
+    cap = out.numel() * out.element_size() // HIT_BYTES
+    st = lib().sphx_intersect_ragged(ctx.handle, _ptr(A), _ptr(B), _ptr(edge_offsets), M, E,
+                                     _ptr(lat_z), _ptr(lat_offsets), L, _ptr(edge_lat_lo),
+                                     _ptr(edge_lat_hi), _mode(mode), _ptr(out), cap,
+                                     _ptr(out_total), _stream(stream))
+    _check(st, "sphx_intersect_ragged")
+
+
+def sphx_autotune_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, out, out_total,
+                         mode="eft", stream=None) -> float:
+    M = int(edge_offsets.shape[0]) - 1
+    E = int(A.shape[0])
+    L = int(lat_z.shape[0])
+    cap = out.numel() * out.element_size() // HIT_BYTES
+    ms = ctypes.c_double(0.0)
+    st = lib().sphx_autotune_ragged(ctx.handle, _ptr(A), _ptr(B), _ptr(edge_offsets), M, E,
+                                    _ptr(lat_z), _ptr(lat_offsets), L, _mode(mode), _ptr(out), cap,
+                                    _ptr(out_total), _stream(stream), ctypes.byref(ms))
+    _check(st, "sphx_autotune_ragged")
+    return ms.value
+
+
+def hits_to_numpy(out, total: int):
+    """View the first `total` records of a ragged output buffer as a numpy structured array."""
+    import numpy as np
+    raw = out.view(torch.uint8)[: int(total) * HIT_BYTES].cpu().numpy()
+    return raw.view(np.dtype(HIT_DTYPE))
+
+
+PIPE_FP32, PIPE_FP64, PIPE_INT32 = 0, 1, 2
+
+
+def sphx_probe_fma_rate(pipe) -> float:
+    """Measured throughput of a pipe: FP32 / FP64 FMA in flop/s (an FMA counts
+    2), or 32-bit integer multiply-adds per second (pipe 2). A bool selects
+    FP64 (True) or FP32 (False)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().sphx_probe_fma_rate(int(pipe), ctypes.byref(v)), "sphx_probe_fma_rate")
+    return v.value

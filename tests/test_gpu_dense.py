@@ -1,0 +1,219 @@
+"""Parity of the dense CUDA call (sphx_intersect_gca_constlat) with the oracle.
+
+Inputs come from the seeded generators; the expected values come from the
+exact-rational oracle (oracle/exact.py) and, for the bit-level checks, from
+the step-by-step FP64 reference of the same algorithms (oracle/accux_ref.c),
+which performs the same correctly rounded operations in the same order:
+  * FP64-EFT (AccuX, Algorithm 8, renormalised AccuDOP) and direct FP64
+    (Sec. 4) must equal the step reference bit for bit, counts included;
+  * FP64-EFT must match the oracle's hit counts exactly on every arc the oracle
+    does not flag as near a boundary, and each point within 4 ulp per
+    component (rule in tests/parity.py);
+  * float-float must match the counts and stay within its stated bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import steps
+from paper_2510_09892_gb300 import sphx
+from paper_2510_09892_gb300 import workloads as W
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+# float-float's stated bound (s^2 carries about 48 bits, so its absolute error
+# near 2^-48 |n|^2 is amplified by 1 / (2 s) near tangency and near the poles):
+#   |P~ - P| <= FF_C * (2^-44 sqrt(1 - z0^2) + 2^-48 |n|^2 / (|n_xy| s))
+FF_C = 2.0
+
+
+def run(A, B, z, mode):
+    dev = torch.device("cuda:0")
+    tA = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
+    tB = torch.from_numpy(np.ascontiguousarray(B)).to(dev)
+    tz = torch.from_numpy(np.ascontiguousarray(z)).to(dev)
+    pts = torch.full((len(z), 2, 3), 7.0, dtype=torch.float64, device=dev)  # poison
+    cnt = torch.full((len(z),), -99, dtype=torch.int32, device=dev)
+    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, mode)
+    torch.cuda.synchronize()
+    return cnt.cpu().numpy(), pts.cpu().numpy()
+
+
+def check_against_exact(cnt, pts, A, B, z, ulp_gate=4.0):
+    ce, pe, fe = P.run_exact(A, B, z)
+    ok = fe == 0
+    assert np.array_equal(cnt[ok], ce[ok]), np.flatnonzero((cnt != ce) & ok)[:10]
+    hit = np.isfinite(pe[..., 0]) & ok[:, None]
+    assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
+    _, _, gate = P.component_errors(pts, pe, z)
+    worst = np.nanmax(np.where(hit[..., None], gate, 0.0))
+    assert worst <= ulp_gate, worst
+    return ce, pe, fe
+
+
+@pytest.mark.parametrize("n", [1, 5, 127, 128, 129, 1000, 10_000])
+def test_eft_uniform_bit_exact_and_within_4ulp(n):
+    A, B, z = W.uniform_arcs(n, seed=100 + n)
+    cnt, pts = run(A, B, z, "eft")
+    cr, pr = steps.accux(A, B, z, variant=2)
+    assert np.array_equal(cnt, cr)
+    assert P.same_bits(pts, pr)
+    check_against_exact(cnt, pts, A, B, z)
+
+
+def test_direct_uniform_bit_exact_with_step_reference():
+    A, B, z = W.uniform_arcs(10_000)
+    cnt, pts = run(A, B, z, "direct")
+    cr, pr = steps.direct(A, B, z)
+    assert np.array_equal(cnt, cr)
+    assert P.same_bits(pts, pr)
+
+
+def test_printed_variant_bit_exact_with_step_reference():
+    A, B, z = W.stress_arcs(5000, seed=7)
+    cnt, pts = run(A, B, z, "eft_printed")
+    cr, pr = steps.accux(A, B, z, variant=0)
+    assert np.array_equal(cnt, cr)
+    assert P.same_bits(pts, pr)
+
+
+def test_eft_stress_mix_within_4ulp_and_direct_worse():
+    A, B, z, k = W.stress_arcs(20_000, seed=11, return_class=True)
+    cnt, pts = run(A, B, z, "eft")
+    cr, pr = steps.accux(A, B, z, variant=2)
+    assert np.array_equal(cnt, cr) and P.same_bits(pts, pr)
+    ce, pe, fe = check_against_exact(cnt, pts, A, B, z)
+    # the paper's norm metric stays within its bound 3 sqrt(1 - z0^2) u (Sec. 6.2)
+    ok = (fe == 0)[:, None] & np.isfinite(pe[..., 0])
+    assert np.nanmax(np.where(ok, P.norm_error(pts, pe, z), 0)) <= 3.0
+    # direct FP64 loses about half the digits on this mix (Sec. 4)
+    cd, pd = run(A, B, z, "direct")
+    both = ok & np.isfinite(pd[..., 0])
+    assert np.nanmax(np.where(both, P.norm_error(pd, pe, z), 0)) > 1e3
+
+
+def _ff_bound(A, B, z):
+    """Stated float-float bound in units of u sqrt(1 - z0^2) (the norm_error unit)."""
+    n = np.cross(A, B)
+    nxy = np.hypot(n[:, 0], n[:, 1])
+    S3 = (n ** 2).sum(1)
+    s = np.sqrt(np.maximum(nxy ** 2 - S3 * z * z, 0))
+    rho = np.sqrt(np.maximum(0.0, (1 - z) * (1 + z)))
+    with np.errstate(divide="ignore"):
+        b = FF_C * (2.0 ** -44 * rho + 2.0 ** -48 * S3 / (nxy * s))
+    return b / (P.U * np.maximum(rho, 1e-300))
+
+
+@pytest.mark.parametrize("gen", ["uniform", "stress"])
+def test_ff32_within_stated_bound(gen):
+    if gen == "uniform":
+        A, B, z = W.uniform_arcs(10_000, seed=31)
+    else:
+        A, B, z = W.stress_arcs(10_000, seed=32)
+    cnt, pts = run(A, B, z, "ff32")
+    ce, pe, fe = P.run_exact(A, B, z)
+    ok = fe == 0
+    bound = _ff_bound(A, B, z)
+    hit = np.isfinite(pe[..., 0]) & np.isfinite(pts[..., 0]) & ok[:, None]
+    err = P.norm_error(pts, pe, z)
+    assert (np.where(hit, err, 0) <= bound[:, None]).all()
+    # counts may differ only where float-float cannot resolve the sign of s^2
+    # or an endpoint tie: near-tangent and near-pole arcs of the stress mix
+    mism = (cnt != ce) & ok
+    assert mism.mean() <= (0.03 if gen == "stress" else 0.0)
+
+
+def test_edge_cases():
+    nan, inf = float("nan"), float("inf")
+    e = np.array([1.0, 0.0, 0.0])
+    rows = [
+        # (x1, x2, z0, expected count)
+        (e, e, 0.3, -1),                                  # x1 == x2: n = 0
+        (e, -e, 0.0, -1),                                 # antipodal: n = 0
+        (e, [0.0, 1.0, 0.0], 0.0, -1),                    # on the equator, z0 = 0
+        (e, [0.0, 1.0, 0.0], 0.5, 0),                     # on the equator, z0 != 0
+        ([nan, 0, 1], e, 0.1, 0),                         # NaN input
+        (e, [0.0, 0.0, 1.0], inf, 0),                     # infinite z0
+        ([0.6, 0.0, 0.8], [0.0, 0.6, 0.8], 0.8, 2),       # both endpoints on the latitude
+        ([0.6, 0.0, 0.8], [0.0, 0.6, 0.8], 0.9, 0),       # above the great circle's top
+        ([1.0, 0.0, 0.0], [0.0, 0.0, 1.0], 1.0, 1),       # meridian arc to the pole: tangent at the pole
+        ([1.0, 0.0, 0.0], [0.0, 0.0, 1.0], 0.0, 1),       # meridian arc through the equator endpoint
+        ([2.0, 0.0, 0.0], [0.0, 0.0, 3.0], 0.5, 1),       # non-unit endpoints
+    ]
+    A = np.array([r[0] for r in rows], dtype=np.float64)
+    B = np.array([r[1] for r in rows], dtype=np.float64)
+    z = np.array([r[2] for r in rows], dtype=np.float64)
+    from oracle import exact
+    want = np.array([exact.intersect(A[i], B[i], z[i]).count for i in range(len(z))])
+    for mode in ("eft", "direct", "ff32"):
+        cnt, pts = run(A, B, z, mode)
+        # degenerate, non-finite and equator cases are exact decisions in every mode
+        assert np.array_equal(cnt[:6], want[:6]), (mode, cnt, want)
+        assert np.isnan(pts[:6]).all()
+        # exactly max(count, 0) slots hold a point, the others are NaN
+        filled = np.isfinite(pts).all(axis=2).sum(axis=1)
+        assert np.array_equal(filled, np.maximum(cnt, 0))
+        assert (np.isfinite(pts).all(axis=2) | np.isnan(pts).all(axis=2)).all()
+    cnt, pts = run(A, B, z, "eft")
+    assert np.array_equal(cnt, want)
+
+
+def test_n_zero_and_bad_arguments():
+    dev = torch.device("cuda:0")
+    z = torch.zeros(0, dtype=torch.float64, device=dev)
+    A = torch.zeros((0, 3), dtype=torch.float64, device=dev)
+    pts = torch.zeros((0, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(0, dtype=torch.int32, device=dev)
+    sphx.sphx_intersect_gca_constlat(A, A, z, pts, cnt, "eft")  # no-op
+    L = sphx.lib()
+    A = torch.zeros((64, 3), dtype=torch.float64, device=dev)
+    z = torch.zeros(64, dtype=torch.float64, device=dev)
+    pts = torch.zeros((64, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(64, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+    p = A.data_ptr()
+    assert L.sphx_intersect_gca_constlat(p, p, z.data_ptr(), 64, pts.data_ptr(), cnt.data_ptr(),
+                                         9, s) == sphx.ERR_INVALID_ARG
+    assert L.sphx_intersect_gca_constlat(p + 8, p, z.data_ptr(), 63, pts.data_ptr(),
+                                         cnt.data_ptr(), 1, s) == sphx.ERR_INVALID_ARG
+    assert L.sphx_intersect_gca_constlat(p, p, z.data_ptr(), -1, pts.data_ptr(), cnt.data_ptr(),
+                                         1, s) == sphx.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+
+
+def test_graph_capture_replays_dense_call():
+    A, B, z = W.uniform_arcs(4096, seed=5)
+    dev = torch.device("cuda:0")
+    tA, tB, tz = (torch.from_numpy(v).to(dev) for v in (A, B, z))
+    pts = torch.empty((4096, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.empty(4096, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "eft", s)  # warm-up
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "eft", s)
+    pts.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    cr, pr = steps.accux(A, B, z, variant=2)
+    assert np.array_equal(cnt.cpu().numpy(), cr)
+    assert P.same_bits(pts.cpu().numpy(), pr)
+
+
+def test_full_size_stress_workload_sampled():
+    """The 10^6-arc ill-conditioned workload in the benchmark's launch shape:
+    every arc bit-exact with the step reference, a seeded sample of 20 000
+    arcs against the exact oracle."""
+    A, B, z = W.stress_arcs(1_000_000)
+    cnt, pts = run(A, B, z, "eft")
+    cr, pr = steps.accux(A, B, z, variant=2)
+    assert np.array_equal(cnt, cr)
+    assert P.same_bits(pts, pr)
+    idx = np.sort(np.random.default_rng(0).choice(len(z), 20_000, replace=False))
+    check_against_exact(cnt[idx], pts[idx], A[idx], B[idx], z[idx])
+    cd, pd = run(A, B, z, "direct")
+    cr, pr = steps.direct(A, B, z)
+    assert np.array_equal(cd, cr) and P.same_bits(pd, pr)

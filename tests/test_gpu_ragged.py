@@ -1,0 +1,270 @@
+"""Parity of the ragged CUDA call (sphx_intersect_ragged) with the oracle.
+
+Expected hits come from brute force over EVERY (edge, latitude) pair of each
+mesh, with no candidate pruning:
+  * the step-by-step FP64 reference (oracle/accux_ref.c) on all pairs must
+    give exactly the GPU's records, bit for bit (so the candidate ranges lose
+    no hit and the compaction drops or duplicates none);
+  * the exact oracle (oracle/ragged.py) on the sampled edges must agree on the
+    hits, points within 4 ulp per component.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import exact, steps
+from oracle import ragged as oracle_ragged
+from paper_2510_09892_gb300 import sphx
+from paper_2510_09892_gb300 import workloads as W
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def to_dev(batch):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for k, v in batch.items()}
+
+
+def all_pairs_reference(batch, mode="eft", edges=None):
+    """Brute force with the step reference: records sorted by (edge, lat, root)."""
+    A, B = batch["A"], batch["B"]
+    eo, lo_ = batch["edge_offsets"], batch["lat_offsets"]
+    lat_z = batch["lat_z"]
+    E = len(A)
+    mesh_of = np.searchsorted(eo, np.arange(E), side="right") - 1
+    if edges is None:
+        edges = np.arange(E)
+    nl = (lo_[mesh_of[edges] + 1] - lo_[mesh_of[edges]]).astype(np.int64)
+    pe = np.repeat(edges, nl)
+    first = np.repeat(lo_[mesh_of[edges]], nl)
+    start = np.repeat(np.cumsum(nl) - nl, nl)
+    pk = first + (np.arange(len(pe)) - start)
+    if mode == "eft":
+        c, p = steps.accux(A[pe], B[pe], lat_z[pk], variant=2)
+    else:
+        c, p = steps.direct(A[pe], B[pe], lat_z[pk])
+    recs = []
+    for r in range(2):
+        h = np.isfinite(p[:, r, 0])
+        recs.append(np.stack([pe[h], pk[h], np.full(h.sum(), r)], 1))
+        recs[-1] = (recs[-1], p[h, r, 0], p[h, r, 1])
+    key = np.concatenate([recs[0][0], recs[1][0]])
+    x = np.concatenate([recs[0][1], recs[1][1]])
+    y = np.concatenate([recs[0][2], recs[1][2]])
+    order = np.lexsort((key[:, 2], key[:, 1], key[:, 0]))
+    return key[order], x[order], y[order]
+
+
+def run_ragged(ctx, d, mode="eft", cap=None, lo=None, hi=None):
+    if cap is None:  # room for two hits on every (edge, latitude) pair
+        eo = d["edge_offsets"].cpu().numpy()
+        lo_ = d["lat_offsets"].cpu().numpy()
+        cap = 16 + 2 * int((np.diff(eo) * np.diff(lo_)).sum())
+    out = torch.full((cap * 4,), -1, dtype=torch.int64, device=DEV)  # 32 B records, poisoned
+    total = torch.full((1,), -5, dtype=torch.int64, device=DEV)
+    sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["edge_offsets"], d["lat_z"],
+                               d["lat_offsets"], out, total, mode, lo, hi)
+    st = ctx.sync_status()
+    t = int(total.item())
+    recs = sphx.hits_to_numpy(out, min(t, cap))
+    return st, t, recs
+
+
+def sorted_records(recs):
+    order = np.lexsort((recs["root"], recs["lat"], recs["edge"]))
+    r = recs[order]
+    key = np.stack([r["edge"], r["lat"].astype(np.int64), r["root"].astype(np.int64)], 1)
+    return key, r["x"].copy(), r["y"].copy()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = sphx.Context(0)
+    yield c
+    c.close()
+
+
+def small_batch(seed=3):
+    return W.ragged_meshes(6, 40, 600, seed=seed, lat_min=180, lat_max=500)
+
+
+@pytest.mark.parametrize("compaction", [sphx.COMPACT_ATOMIC, sphx.COMPACT_ORDERED])
+@pytest.mark.parametrize("mode", ["eft", "direct"])
+def test_small_meshes_equal_all_pairs_reference(ctx, mode, compaction):
+    batch = small_batch()
+    d = to_dev(batch)
+    ctx.set_tuning(compaction=compaction, use_graph=1)
+    st, total, recs = run_ragged(ctx, d, mode)
+    assert st == sphx.OK
+    key, x, y = all_pairs_reference(batch, mode)
+    assert total == len(key)
+    if compaction == sphx.COMPACT_ORDERED:
+        got = np.stack([recs["edge"], recs["lat"].astype(np.int64),
+                        recs["root"].astype(np.int64)], 1)
+        gx, gy = recs["x"], recs["y"]
+    else:
+        got, gx, gy = sorted_records(recs)
+    assert np.array_equal(got, key)
+    assert P.same_bits(gx, x) and P.same_bits(gy, y)
+    ctx.reset_tuning()
+
+
+def test_small_meshes_against_exact_oracle(ctx):
+    batch = W.ragged_meshes(4, 20, 120, seed=9, lat_min=180, lat_max=260)
+    d = to_dev(batch)
+    st, total, recs = run_ragged(ctx, d, "eft")
+    assert st == sphx.OK
+    want, flagged, degenerate = oracle_ragged.intersect_ragged(
+        batch["A"], batch["B"], batch["edge_offsets"], batch["lat_z"], batch["lat_offsets"])
+    wk = {(e, k, r): (x, yy) for e, k, r, x, yy in want}
+    gk, gx, gy = sorted_records(recs)
+    got = {tuple(int(v) for v in gk[i]): (gx[i], gy[i]) for i in range(len(gk))}
+    # identical hit sets except on pairs the oracle flags as near a boundary
+    diff = set(wk) ^ set(got)
+    assert all((e, k) in flagged for e, k, _ in diff), sorted(diff)[:5]
+    for key in set(wk) & set(got):
+        e, k, r = key
+        z0 = batch["lat_z"][k]
+        ref = np.array([[[wk[key][0], wk[key][1], z0]] * 2])
+        pts = np.array([[[got[key][0], got[key][1], z0]] * 2])
+        _, _, gate = P.component_errors(pts, ref, np.array([z0]))
+        assert gate.max() <= 4.0, (key, gate)
+
+
+def test_cubed_sphere_with_latlon_grid(ctx):
+    A, B = W.cubed_sphere_edges(8)
+    batch = {"A": A, "B": B, "edge_offsets": np.array([0, len(A)], dtype=np.int64),
+             "lat_z": W.latlon_latitudes(721), "lat_offsets": np.array([0, 721], dtype=np.int64)}
+    d = to_dev(batch)
+    st, total, recs = run_ragged(ctx, d, "eft")
+    assert st == sphx.OK
+    key, x, y = all_pairs_reference(batch)
+    got, gx, gy = sorted_records(recs)
+    assert total == len(key) and np.array_equal(got, key)
+    assert P.same_bits(gx, x) and P.same_bits(gy, y)
+
+
+def test_capacity_overflow_reports_and_truncates(ctx):
+    batch = small_batch(seed=4)
+    d = to_dev(batch)
+    key, x, y = all_pairs_reference(batch)
+    cap = len(key) // 3
+    ctx.set_tuning(compaction=sphx.COMPACT_ORDERED)
+    st, total, recs = run_ragged(ctx, d, "eft", cap=cap)
+    ctx.reset_tuning()
+    assert st == sphx.ERR_CAPACITY
+    assert total == len(key)
+    assert len(recs) == cap
+    got = np.stack([recs["edge"], recs["lat"].astype(np.int64), recs["root"].astype(np.int64)], 1)
+    assert np.array_equal(got, key[:cap])
+    # the status word is cleared once read
+    assert ctx.sync_status() == sphx.OK
+
+
+def test_caller_ranges_and_candidate_ranges(ctx):
+    batch = small_batch(seed=5)
+    d = to_dev(batch)
+    E = len(batch["A"])
+    eo, lo_ = batch["edge_offsets"], batch["lat_offsets"]
+    mesh_of = np.searchsorted(eo, np.arange(E), side="right") - 1
+    full_lo = torch.from_numpy(lo_[mesh_of].astype(np.int32)).to(DEV)
+    full_hi = torch.from_numpy(lo_[mesh_of + 1].astype(np.int32)).to(DEV)
+    st, total, recs = run_ragged(ctx, d, "eft", lo=full_lo, hi=full_hi)
+    assert st == sphx.OK
+    key, x, y = all_pairs_reference(batch)
+    got, gx, gy = sorted_records(recs)
+    assert np.array_equal(got, key) and P.same_bits(gx, x)
+    # the computed ranges cover every hit and are far narrower than the grids
+    lo = torch.empty(E, dtype=torch.int32, device=DEV)
+    hi = torch.empty(E, dtype=torch.int32, device=DEV)
+    sphx.sphx_candidate_ranges(d["A"], d["B"], d["edge_offsets"], d["lat_z"], d["lat_offsets"],
+                               lo, hi)
+    lo, hi = lo.cpu().numpy(), hi.cpu().numpy()
+    e, k = key[:, 0], key[:, 1]
+    assert ((lo[e] <= k) & (k < hi[e])).all()
+    assert ((lo >= lo_[mesh_of]) & (hi <= lo_[mesh_of + 1])).all()
+    assert (hi - lo).sum() < 0.5 * (lo_[mesh_of + 1] - lo_[mesh_of]).sum()
+
+
+def test_empty_batches_and_empty_meshes(ctx):
+    batch = small_batch(seed=6)
+    # insert an empty mesh in the middle
+    eo = batch["edge_offsets"]
+    batch["edge_offsets"] = np.concatenate([eo[:3], eo[2:3], eo[3:]])
+    lo_ = batch["lat_offsets"]
+    batch["lat_offsets"] = np.concatenate([lo_[:3], lo_[2:3] + 0, lo_[3:]])
+    d = to_dev(batch)
+    st, total, recs = run_ragged(ctx, d, "eft")
+    assert st == sphx.OK
+    key, _, _ = all_pairs_reference(batch)
+    assert total == len(key)
+    # E = 0
+    e0 = {"A": torch.zeros((0, 3), dtype=torch.float64, device=DEV),
+          "B": torch.zeros((0, 3), dtype=torch.float64, device=DEV),
+          "edge_offsets": torch.zeros(2, dtype=torch.int64, device=DEV),
+          "lat_z": d["lat_z"], "lat_offsets": d["lat_offsets"][:2].clone()}
+    e0["lat_offsets"][0] = 0
+    st, total, recs = run_ragged(ctx, e0, "eft", cap=16)
+    assert st == sphx.OK and total == 0
+
+
+def test_graph_replay_sees_new_inputs(ctx):
+    b1 = small_batch(seed=7)
+    d = to_dev(b1)
+    st, t1, _ = run_ragged(ctx, d, "eft")
+    # overwrite the endpoints in place (same pointers -> the cached graph replays)
+    b2 = dict(b1)
+    b2["B"] = np.ascontiguousarray(b1["A"][::-1])
+    b2["A"] = np.ascontiguousarray(b1["B"][::-1])
+    d["A"].copy_(torch.from_numpy(b2["A"]))
+    d["B"].copy_(torch.from_numpy(b2["B"]))
+    st, t2, recs = run_ragged(ctx, d, "eft")
+    key, x, y = all_pairs_reference(b2)
+    got, gx, gy = sorted_records(recs)
+    assert st == sphx.OK and np.array_equal(got, key) and P.same_bits(gx, x)
+
+
+def test_autotune_then_correct(ctx):
+    batch = small_batch(seed=8)
+    d = to_dev(batch)
+    # a buffer too small for the batch: the trials overflow it, and the
+    # autotuner must not leave that status behind for the next call
+    out = torch.empty(4 * 8, dtype=torch.int64, device=DEV)
+    total = torch.empty(1, dtype=torch.int64, device=DEV)
+    ms = sphx.sphx_autotune_ragged(ctx, d["A"], d["B"], d["edge_offsets"], d["lat_z"],
+                                   d["lat_offsets"], out, total, "eft")
+    assert ms > 0
+    t = ctx.get_tuning()
+    assert t["threads_per_block"] in (128, 256) and t["use_graph"] == 1
+    assert ctx.sync_status() == sphx.OK
+    st, total, recs = run_ragged(ctx, d, "eft")
+    key, x, y = all_pairs_reference(batch)
+    got, gx, gy = sorted_records(recs)
+    assert st == sphx.OK and np.array_equal(got, key) and P.same_bits(gx, x)
+    ctx.reset_tuning()
+
+
+def test_full_size_cubed_sphere_sampled(ctx):
+    """The regridding workload at full size (N = 1024, 12 595 200 edges, 721
+    latitudes) in the benchmark's launch shape: the records of 3000 seeded
+    sampled edges equal the all-pairs step reference bit for bit, and every
+    record is a valid pair whose point lies on the unit sphere."""
+    A, B = W.cubed_sphere_edges(1024)
+    batch = {"A": A, "B": B, "edge_offsets": np.array([0, len(A)], dtype=np.int64),
+             "lat_z": W.latlon_latitudes(721), "lat_offsets": np.array([0, 721], dtype=np.int64)}
+    d = to_dev(batch)
+    cap = 4 * len(A)
+    st, total, recs = run_ragged(ctx, d, "eft", cap=cap)
+    assert st == sphx.OK
+    sample = np.sort(np.random.default_rng(1).choice(len(A), 3000, replace=False))
+    key, x, y = all_pairs_reference(batch, edges=sample)
+    sel = np.isin(recs["edge"], sample)
+    got, gx, gy = sorted_records(recs[sel])
+    assert np.array_equal(got, key)
+    assert P.same_bits(gx, x) and P.same_bits(gy, y)
+    # every record is a valid pair with a point on its latitude's circle
+    assert (recs["lat"] >= 0).all() and (recs["lat"] < 721).all()
+    z0 = batch["lat_z"][recs["lat"]]
+    r2 = recs["x"] ** 2 + recs["y"] ** 2 + z0 ** 2
+    assert np.abs(r2 - 1).max() < 1e-14
