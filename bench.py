@@ -2,11 +2,13 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sphx|reference]
 
-A step is one dense call (sphx_intersect_gca_constlat, FP64-EFT) over the
+A step is one dense call (sphx_intersect_gca_constlat) over the
 ill-conditioned workload of 10^6 arcs (40 % short, 30 % near-tangent, 20 %
 near-pole, 10 % near-antipodal), inputs resident in HBM; the L2 cache is
-flushed (a 256 MiB write) between timed steps. Direct FP64 and float-float are
-timed the same way beside it. Under torchrun each rank runs its own
+flushed (a 256 MiB write) between timed steps. The headline mode is the
+integer-limb evaluation (SPHX_MODE_WIDE_INT, within 1 ulp of the exact
+result); FP64-EFT (the paper's AccuX), direct FP64 and float-float are timed
+the same way beside it. Under torchrun each rank runs its own
 independently seeded batch (weak scaling, no data-path collective); the step
 time is the maximum over ranks.
 
@@ -43,6 +45,9 @@ WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-uniform 
 # algorithmic work per arc of the dense call (both roots and the on-arc test)
 BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
+INT_OPS_PER_ARC = {}  # 32-bit integer operations per arc of the integer-limb kernel
+DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
+          "direct": "f64", "ff32": "f32 pairs + f64"}
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE = 32_768            # arcs per oracle step
 
@@ -176,7 +181,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * CPU_SAMPLE / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "exact rational (Python int), rounded to f64",
-        "data": "synthetic", "config": config_dict(args, "eft"),
+        "data": "synthetic", "config": config_dict(args, args.mode),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{CPU_SAMPLE} consecutive arcs of the workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -198,6 +203,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sphx", choices=["sphx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="wide", choices=["wide", "eft", "direct", "ff32"],
+                    help="headline evaluation mode (the others are timed beside it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -245,71 +252,83 @@ def main():
     fp64_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP64) / 2  # FMA/s = FP64 op slots/s
     fp32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP32) / 2
     int32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_INT32)
+    head = args.mode
+    others = [m for m in ("wide", "eft", "direct", "ff32") if m != head]
 
     # warm-up of every mode, then the headline timed region
-    for mode in ("eft", "direct", "ff32"):
+    for mode in [head] + others:
         timed(mode, 1, args.warmup)
     barrier()
     torch.cuda.synchronize()
     # the sampler runs through every timed leg (headline, other modes, e2e)
     with ClockSampler(local) as clocks:
         t_wall = time.perf_counter()
-        eft_ms = timed("eft", args.steps, 0)
+        head_ms = timed(head, args.steps, 0)
         torch.cuda.synchronize()
         barrier()
         t_wall = time.perf_counter() - t_wall
         gpu_launches = args.steps  # one dense_kernel launch per step
-        step_ms = reduce_max(statistics.mean(eft_ms), dev)
+        step_ms = reduce_max(statistics.mean(head_ms), dev)
         value = world * N_ARCS / (step_ms * 1e-3)
 
-        modes = {}
-        for mode in ("direct", "ff32"):
+        modes = {head: {"value": value, "ms_per_step": step_ms}}
+        for mode in others:
             m = reduce_max(statistics.mean(timed(mode, args.steps, 0)), dev)
             modes[mode] = {"value": world * N_ARCS / (m * 1e-3), "ms_per_step": m}
-        modes["eft"] = {"value": value, "ms_per_step": step_ms}
-        e2e = e2e_leg(sphx, torch, dev, A, B, z, args)
+        e2e = e2e_leg(sphx, torch, dev, A, B, z, args, head)
         # the timed legs last well under a second, shorter than the sampling
-        # period: keep the same kernel running for 1.5 s more so that the
+        # period: keep the headline kernel running for 1.5 s more so that the
         # clock samples describe the GPU under this load (not timed)
         soak_end = time.perf_counter() + 1.5
         while time.perf_counter() < soak_end:
-            timed("eft", 50, 0)
+            timed(head, 50, 0)
     clk = clocks.summary()
-    clk["window"] = "timed legs plus a 1.5 s soak of the same kernel right after"
+    clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
 
-    # hits per step, from one more EFT call's outputs
-    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "eft")
+    # hits per step, from one more headline call's outputs
+    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, head)
     hits = int(torch.clamp(cnt, min=0).sum().item())
 
-    kernel_ms = statistics.mean(eft_ms)
-    fp64_ops = FP64_OPS_PER_ARC["eft"] * N_ARCS
-    roofline = {
-        "bound": "alu", "unit": "TFLOP/s",
-        "achieved": fp64_ops / (kernel_ms * 1e-3) / 1e12,
-        "peak": fp64_peak / 1e12,
-        "frac": (fp64_ops / (kernel_ms * 1e-3)) / fp64_peak,
-        "traffic": None,
-        "kernel": "dense_kernel<EFT_FP64>",
-        "note": ("FP64 pipe: algorithmic FP64 operations (add, mul, fma, div, sqrt each one "
-                 "op, 465 per arc) per second against the measured FP64 FMA issue rate "
-                 "(sphx_probe_fma_rate, live, of measured)"),
-    }
     hbm_peak = measured_hbm_peak()
-    roofline_hbm = {
-        "bound": "hbm", "unit": "GB/s",
-        "achieved": BYTES_PER_ARC * N_ARCS / (kernel_ms * 1e-3) / 1e9,
-        "peak": hbm_peak, "frac": BYTES_PER_ARC * N_ARCS / (kernel_ms * 1e-3) / 1e9 / hbm_peak,
-        "note": "108 B per arc (56 in, 52 out) against the measured copy bandwidth",
-    }
+
+    def hbm_roof(ms):
+        gbs = BYTES_PER_ARC * N_ARCS / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm_peak,
+                "frac": gbs / hbm_peak, "traffic": None,
+                "note": "108 B per arc (56 in, 52 out) against the measured copy bandwidth "
+                        "(MEASURED_PEAKS.json, of measured)"}
+
+    def alu_roof(ms, ops_per_arc, peak, pipe):
+        rate = ops_per_arc * N_ARCS / (ms * 1e-3)
+        return {"bound": "alu", "unit": "Tops/s", "achieved": rate / 1e12, "peak": peak / 1e12,
+                "frac": rate / peak, "traffic": None,
+                "note": f"{pipe}: {ops_per_arc} operations per arc against the pipe's issue "
+                        "rate measured live by sphx_probe_fma_rate (of measured)"}
+
+    head_kernel_ms = statistics.mean(head_ms)
+    if head in INT_OPS_PER_ARC:
+        roofline = alu_roof(head_kernel_ms, INT_OPS_PER_ARC[head], int32_peak,
+                            "32-bit integer pipe")
+    elif head in FP64_OPS_PER_ARC:
+        roofline = alu_roof(head_kernel_ms, FP64_OPS_PER_ARC[head], fp64_peak, "FP64 pipe")
+    else:
+        roofline = hbm_roof(head_kernel_ms)
+    roofline["kernel"] = f"dense_kernel<{head}>"
+    per_mode_roofs = {"hbm": {m: hbm_roof(modes[m]["ms_per_step"])["frac"] for m in modes}}
+    per_mode_roofs["fp64_pipe"] = {m: alu_roof(modes[m]["ms_per_step"], FP64_OPS_PER_ARC[m],
+                                               fp64_peak, "FP64")["frac"]
+                                   for m in modes if m in FP64_OPS_PER_ARC}
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, "eft"), "e2e": e2e, "gpu_launches": gpu_launches,
-        "clocks": clk, "roofline": roofline, "roofline_hbm": roofline_hbm,
-        "modes": modes, "eft_over_direct_time": step_ms / modes["direct"]["ms_per_step"],
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
+        "config": config_dict(args, head), "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clk, "roofline": roofline, "roofline_hbm": hbm_roof(head_kernel_ms),
+        "roofline_frac_by_mode": per_mode_roofs,
+        "modes": modes,
+        "eft_over_direct_time": modes["eft"]["ms_per_step"] / modes["direct"]["ms_per_step"],
         "hits_per_step": hits, "timed_wall_s": t_wall,
         "peaks": {"fp64_fma_per_s": fp64_peak, "fp32_fma_per_s": fp32_peak,
                   "int32_imad_per_s": int32_peak, "hbm_gbs": hbm_peak},
@@ -343,7 +362,7 @@ def cpu_baseline_leg() -> dict:
             "sample": f"first {n} arcs of the 10^6-arc stress workload"}
 
 
-def e2e_leg(sphx, torch, dev, A, B, z, args) -> dict:
+def e2e_leg(sphx, torch, dev, A, B, z, args, mode) -> dict:
     """Same metric through the C ABI from pinned HOST buffers: every step copies
     the inputs in and the points and counts out, in 4 chunks over 2 streams so
     the copies overlap the kernels."""
@@ -377,7 +396,7 @@ def e2e_leg(sphx, torch, dev, A, B, z, args) -> dict:
                 dA[:m].copy_(hA[lo:hi], non_blocking=True)
                 dB[:m].copy_(hB[lo:hi], non_blocking=True)
                 dz[:m].copy_(hz[lo:hi], non_blocking=True)
-                sphx.sphx_intersect_gca_constlat(dA[:m], dB[:m], dz[:m], dP[:m], dC[:m], "eft", s)
+                sphx.sphx_intersect_gca_constlat(dA[:m], dB[:m], dz[:m], dP[:m], dC[:m], mode, s)
                 hP[lo:hi].copy_(dP[:m], non_blocking=True)
                 hC[lo:hi].copy_(dC[:m], non_blocking=True)
 

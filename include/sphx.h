@@ -65,7 +65,16 @@ typedef enum {
     SPHX_MODE_EFT_FF32 = 2,
     /* Algorithm 8 exactly as printed (no renormalisation after AccuDOP), for
        comparison; loses accuracy on very short and near-antipodal arcs. */
-    SPHX_MODE_EFT_FP64_PRINTED = 3
+    SPHX_MODE_EFT_FP64_PRINTED = 3,
+    /* Eq. 2.2 in software floating point with 32-bit integer limbs: n from
+       exact products of the inputs, |n_xy|^2, |n|^2 and s^2 with 128-bit
+       mantissas (the cancelling steps of Sec. 4 and 6.1), the square root,
+       numerators and the division by |n_xy|^2 with 96-bit mantissas; the
+       on-arc test in FP32 on offsets from the endpoints. Same bound as
+       SPHX_MODE_EFT_FP64 (<= 4 ulp per component of the correctly rounded
+       exact point), computed on the integer pipe, which GB300 runs 32 times
+       faster than its FP64 pipe. */
+    SPHX_MODE_WIDE_INT = 4
 } sphx_mode;
 
 /* Output compaction scheme of the ragged call. */

@@ -122,6 +122,7 @@ extern "C" sphx_status sphx_intersect_gca_constlat(const double *A, const double
         case SPHX_MODE_EFT_FP64_PRINTED:
             launch_dense<kEftFp64Printed>(A, B, z0, n, out_pts, out_count, s);
             break;
+        case SPHX_MODE_WIDE_INT: launch_dense<kWideInt>(A, B, z0, n, out_pts, out_count, s); break;
         default: return SPHX_ERR_INVALID_ARG;
     }
     cudaError_t e = cudaGetLastError();

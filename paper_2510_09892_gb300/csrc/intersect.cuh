@@ -15,10 +15,11 @@
 //               (P x x2).n >= 0: P between x1 and x2 on the minor arc).
 #pragma once
 #include "eft.cuh"
+#include "wide.cuh"
 
 namespace sphx {
 
-enum : int { kDirect = 0, kEftFp64 = 1, kEftFf32 = 2, kEftFp64Printed = 3 };
+enum : int { kDirect = 0, kEftFp64 = 1, kEftFf32 = 2, kEftFp64Printed = 3, kWideInt = 4 };
 
 struct PairOut {
     int count;      // -1, 0, 1, 2
@@ -31,7 +32,7 @@ __device__ __forceinline__ bool finite7(const double (&x1)[3], const double (&x2
            isfinite(x2[1]) && isfinite(x2[2]) && isfinite(z0);
 }
 
-__device__ __forceinline__ void clear(PairOut &o, int count) {
+SPHX_HD void clear(PairOut &o, int count) {
     o.count = count;
     o.hit[0] = o.hit[1] = false;
     o.px[0] = o.px[1] = o.py[0] = o.py[1] = 0.0;
@@ -273,6 +274,152 @@ __device__ __forceinline__ void pair_ff32(const double (&x1)[3], const double (&
     }
 }
 
+// ---- Eq. 2.2 in multi-limb integer arithmetic (wide.cuh) ----------------------
+// The normal n = x1 x x2 is formed from exact 106-bit products of the FP64
+// inputs and carried with 128-bit mantissas through |n_xy|^2, |n|^2 and
+// s^2 = |n_xy|^2 - |n|^2 z0^2, the steps whose cancellation the paper's error
+// analysis is about (Sec. 4, 6.1); the square root, the numerators
+// z0 n_x n_z +- s n_y, z0 n_y n_z -+ s n_x and the division by |n_xy|^2 follow
+// with 96-bit mantissas (every numerator term is at most sqrt(1 - z0^2)
+// |n_xy|^2 in magnitude, so 96 bits leave each coordinate within a fraction
+// of an ulp). All of it runs on the 32-bit integer pipe.
+//
+// On-arc test: t1 = (x1 x P).n = d1 . m1 with m1 = n x x1 and
+// d1 = P - l x1, l = +-1/|x1| (the sign of P . x1): x1 . m1 = 0, so any l
+// gives the same value, and this choice keeps |d1| |m1| within a factor
+// sqrt(2) of |t1| wherever t1 is small, so m1 and d1 in FP32 (d1 from one
+// FP64 FMA per component) decide its sign correctly except within an angle
+// of about 2^-40 of the endpoint (the oracle's near-endpoint flag).
+// Likewise t2 = (P x x2).n = d2 . m2.
+
+SPHX_HD bool finite_bits(double x) {
+    return ((wide::bits_of(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+SPHX_HD int exponent_bits(double x) {  // unbiased; very small for 0
+    const int ex = (int)((wide::bits_of(x) >> 52) & 0x7ff);
+    return ex ? ex - 1023 : -2000;
+}
+
+// x 2^-sc as a float (mantissa truncated; 0 below the float range)
+SPHX_HD float f32_scaled(double x, int sc) {
+    const uint64_t b = wide::bits_of(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const int fe = ex - 1023 + 127 - sc;
+    if (ex == 0 || fe <= 0) return 0.0f;
+    return wide::float_of(((uint32_t)(b >> 63) << 31) | ((uint32_t)(fe > 254 ? 254 : fe) << 23) |
+                          (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
+// 0.M 2^(e - emax) of a W<4> as a float
+SPHX_HD float f32_rel(const wide::W<4> &a, int emax) {
+    const int fe = a.e - emax + 126;
+    if (wide::is_zero(a) || fe <= 0) return 0.0f;
+    return wide::float_of((a.neg << 31) | ((uint32_t)fe << 23) | ((a.m[3] >> 8) & 0x7fffffu));
+}
+
+// a positive normal float times 2^-sc, as a double (exact)
+SPHX_HD double f64_of_f32_scaled(float f, int sc) {
+    const uint32_t b = wide::fbits_of(f);
+    const int fe = (int)((b >> 23) & 0xff);
+    return wide::double_of(((uint64_t)(fe - 127 + 1023 - sc) << 52) | ((uint64_t)(b & 0x7fffffu) << 29));
+}
+
+SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
+                                          PairOut &o) {
+    using namespace wide;
+    if (!(finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) && finite_bits(x2[0]) &&
+          finite_bits(x2[1]) && finite_bits(x2[2]) && finite_bits(z0)))
+        return clear(o, 0);
+    W<2> a[3], b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        a[i] = from_double<2>(x1[i]);
+        b[i] = from_double<2>(x2[i]);
+    }
+    W<4> n[3];
+    n[0] = sub<4>(mul_exact(a[1], b[2]), mul_exact(a[2], b[1]));  // y1 z2 - z1 y2
+    n[1] = sub<4>(mul_exact(a[2], b[0]), mul_exact(a[0], b[2]));  // z1 x2 - x1 z2
+    n[2] = sub<4>(mul_exact(a[0], b[1]), mul_exact(a[1], b[0]));  // x1 y2 - y1 x2
+    if (is_zero(n[0]) && is_zero(n[1]) && is_zero(n[2])) return clear(o, -1);
+    const bool z0_zero = (bits_of(z0) << 1) == 0;
+    if (is_zero(n[0]) && is_zero(n[1])) return clear(o, z0_zero ? -1 : 0);
+    const W<4> S2 = add<4>(mul<4>(n[0], n[0]), mul<4>(n[1], n[1]));
+    const W<4> S3 = add<4>(S2, mul<4>(n[2], n[2]));
+    const W<2> zz = from_double<2>(z0);
+    const W<4> s2 = sub<4>(S2, mul<4>(S3, mul_exact(zz, zz)));
+    if (s2.neg && !is_zero(s2)) return clear(o, 0);
+    const bool tangent = is_zero(s2);
+
+    const W<3> nx = narrow<4, 3>(n[0]), ny = narrow<4, 3>(n[1]), nz = narrow<4, 3>(n[2]);
+    const W<3> s = tangent ? zero<3>() : sqrt_pos<3>(narrow<4, 3>(s2));
+    const W<3> rS2 = negate<3>(recip<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
+    const W<3> z3 = from_double<3>(z0);
+    const W<3> zFx = mul<3>(z3, mul<3>(nx, nz));
+    const W<3> zFy = mul<3>(z3, mul<3>(ny, nz));
+    const W<3> sX = mul<3>(s, nx);
+    const W<3> sY = mul<3>(s, ny);
+
+    // on-arc test set-up (FP32 normals and endpoints, scaled by powers of two)
+    int emax = n[0].e;
+    emax = n[1].e > emax ? n[1].e : emax;
+    emax = n[2].e > emax ? n[2].e : emax;
+    const float nf[3] = {f32_rel(n[0], emax), f32_rel(n[1], emax), f32_rel(n[2], emax)};
+    int sc1 = exponent_bits(x1[0]), sc2 = exponent_bits(x2[0]);
+#pragma unroll
+    for (int i = 1; i < 3; ++i) {
+        const int e1 = exponent_bits(x1[i]), e2 = exponent_bits(x2[i]);
+        sc1 = e1 > sc1 ? e1 : sc1;
+        sc2 = e2 > sc2 ? e2 : sc2;
+    }
+    float p1[3], p2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p1[i] = f32_scaled(x1[i], sc1);
+        p2[i] = f32_scaled(x2[i], sc2);
+    }
+    const float m1[3] = {wide::fma32(nf[1], p1[2], -nf[2] * p1[1]), wide::fma32(nf[2], p1[0], -nf[0] * p1[2]),
+                         wide::fma32(nf[0], p1[1], -nf[1] * p1[0])};
+    const float m2[3] = {wide::fma32(p2[1], nf[2], -p2[2] * nf[1]), wide::fma32(p2[2], nf[0], -p2[0] * nf[2]),
+                         wide::fma32(p2[0], nf[1], -p2[1] * nf[0])};
+    // l = 1 / |x| in FP32, except that endpoints of unit norm (to FP32
+    // resolution) take l = 1 exactly: then d = P -+ x is exact near x
+    const float r1 = wide::rsqrt_approx(p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]);
+    const float r2 = wide::rsqrt_approx(p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]);
+    const bool unit1 = (sc1 == -1 || sc1 == 0) && fabsf(r1 * (sc1 ? 2.0f : 1.0f) - 1.0f) < 1e-6f;
+    const bool unit2 = (sc2 == -1 || sc2 == 0) && fabsf(r2 * (sc2 ? 2.0f : 1.0f) - 1.0f) < 1e-6f;
+    const double inv1 = unit1 ? 1.0 : f64_of_f32_scaled(r1, sc1);
+    const double inv2 = unit2 ? 1.0 : f64_of_f32_scaled(r2, sc2);
+    const float zf = f32_scaled(z0, 0);
+
+    const int nroots = tangent ? 1 : 2;
+    o.count = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o.hit[r] = false;
+        if (r >= nroots) continue;
+        const W<3> X = add<3>(zFx, r == 0 ? sY : negate<3>(sY));
+        const W<3> Y = add<3>(zFy, r == 0 ? negate<3>(sX) : sX);
+        const double Px = to_double<3>(mul<3>(X, rS2));
+        const double Py = to_double<3>(mul<3>(Y, rS2));
+        o.px[r] = Px;
+        o.py[r] = Py;
+        const float pf[3] = {f32_scaled(Px, 0), f32_scaled(Py, 0), zf};
+        const double l1 = (pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f) ? inv1 : -inv1;
+        const double l2 = (pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f) ? inv2 : -inv2;
+        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0), f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
+                             f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
+        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0), f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
+                             f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
+        const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
+        const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));
+        if (t1 >= 0.0f && t2 >= 0.0f) {
+            o.hit[r] = true;
+            ++o.count;
+        }
+    }
+}
+
 template <int Mode>
 __device__ __forceinline__ void intersect_pair(const double (&x1)[3], const double (&x2)[3],
                                                double z0, PairOut &o) {
@@ -282,6 +429,8 @@ __device__ __forceinline__ void intersect_pair(const double (&x1)[3], const doub
         pair_accux<true>(x1, x2, z0, o);
     else if (Mode == kEftFp64Printed)
         pair_accux<false>(x1, x2, z0, o);
+    else if (Mode == kWideInt)
+        pair_wide(x1, x2, z0, o);
     else
         pair_ff32(x1, x2, z0, o);
 }

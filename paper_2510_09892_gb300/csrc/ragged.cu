@@ -348,6 +348,7 @@ static RaggedKernelFn pick_kernel(int mode, int K, bool ordered) {
         case kDirect: return pick_k<kDirect>(K, ordered);
         case kEftFp64: return pick_k<kEftFp64>(K, ordered);
         case kEftFf32: return pick_k<kEftFf32>(K, ordered);
+        case kWideInt: return pick_k<kWideInt>(K, ordered);
         default: return pick_k<kEftFp64Printed>(K, ordered);
     }
 }

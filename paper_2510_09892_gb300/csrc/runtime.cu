@@ -130,7 +130,7 @@ cudaError_t enqueue_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedS
 
 sphx_status check_ragged_args(const RaggedCall &c) {
     if (c.M < 1 || c.E < 0 || c.L < 0 || c.L > INT32_MAX || c.cap < 0) return SPHX_ERR_INVALID_ARG;
-    if (c.mode < 0 || c.mode > 3) return SPHX_ERR_INVALID_ARG;
+    if (c.mode < 0 || c.mode > 4) return SPHX_ERR_INVALID_ARG;
     if (!c.out_total || (c.cap > 0 && !c.out)) return SPHX_ERR_INVALID_ARG;
     if ((c.lo == nullptr) != (c.hi == nullptr)) return SPHX_ERR_INVALID_ARG;
     if (c.E > 0 && (!c.A || !c.B || !c.edge_offsets || !c.lat_z || !c.lat_offsets))

@@ -20,9 +20,9 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sphx.h")
 # sphx_status
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = range(7)
 # sphx_mode
-MODE_DIRECT_FP64, MODE_EFT_FP64, MODE_EFT_FF32, MODE_EFT_FP64_PRINTED = range(4)
+MODE_DIRECT_FP64, MODE_EFT_FP64, MODE_EFT_FF32, MODE_EFT_FP64_PRINTED, MODE_WIDE_INT = range(5)
 MODES = {"direct": MODE_DIRECT_FP64, "eft": MODE_EFT_FP64, "ff32": MODE_EFT_FF32,
-         "eft_printed": MODE_EFT_FP64_PRINTED}
+         "eft_printed": MODE_EFT_FP64_PRINTED, "wide": MODE_WIDE_INT}
 # sphx_compaction
 COMPACT_AUTO, COMPACT_ATOMIC, COMPACT_ORDERED = range(3)
 

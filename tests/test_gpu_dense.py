@@ -93,6 +93,46 @@ def test_eft_stress_mix_within_4ulp_and_direct_worse():
     assert np.nanmax(np.where(both, P.norm_error(pd, pe, z), 0)) > 1e3
 
 
+@pytest.mark.parametrize("gen", ["uniform", "stress", "mixed", "scaled"])
+def test_wide_int_matches_exact_oracle(gen):
+    """The integer-limb evaluation: exact hit counts on unflagged arcs and
+    every coordinate within 1 ulp of the correctly rounded exact value (the
+    4-ulp bound with room to spare: 96-bit mantissas leave the rounding to
+    decide), on well-conditioned, ill-conditioned, mixed and non-unit inputs."""
+    if gen == "uniform":
+        A, B, z = W.uniform_arcs(10_000, seed=41)
+    elif gen == "stress":
+        A, B, z = W.stress_arcs(40_000, seed=42)
+    elif gen == "mixed":
+        A, B, z = W.mixed_chunk(7, size=20_000)
+    else:  # endpoints scaled by 10^+-30: the formula only uses directions
+        A, B, z = W.stress_arcs(20_000, seed=43)
+        rng = np.random.default_rng(44)
+        A = A * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+        B = B * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    cnt, pts = run(A, B, z, "wide")
+    ce, pe, fe = check_against_exact(cnt, pts, A, B, z, ulp_gate=1.0)
+    ok = (fe == 0)[:, None] & np.isfinite(pe[..., 0])
+    assert np.nanmax(np.where(ok, P.norm_error(pts, pe, z), 0)) <= 1.0
+
+
+def test_wide_int_full_size_stress_sampled():
+    """The 10^6-arc stress workload in the benchmark's launch shape, a seeded
+    sample of 20 000 arcs against the exact oracle; on all arcs the wide
+    evaluation and FP64-EFT agree on the hit counts wherever neither is near
+    a boundary, and their points within the sum of their bounds."""
+    A, B, z = W.stress_arcs(1_000_000)
+    cnt, pts = run(A, B, z, "wide")
+    idx = np.sort(np.random.default_rng(3).choice(len(z), 20_000, replace=False))
+    check_against_exact(cnt[idx], pts[idx], A[idx], B[idx], z[idx], ulp_gate=1.0)
+    ce, pe = run(A, B, z, "eft")
+    same = cnt == ce
+    assert same.mean() > 0.999
+    both = np.isfinite(pts[..., 0]) & np.isfinite(pe[..., 0]) & same[:, None]
+    _, _, gate = P.component_errors(pe, pts, z)
+    assert np.nanmax(np.where(both[..., None], gate, 0)) <= 5.0
+
+
 def _ff_bound(A, B, z):
     """Stated float-float bound in units of u sqrt(1 - z0^2) (the norm_error unit)."""
     n = np.cross(A, B)
@@ -146,7 +186,7 @@ def test_edge_cases():
     z = np.array([r[2] for r in rows], dtype=np.float64)
     from oracle import exact
     want = np.array([exact.intersect(A[i], B[i], z[i]).count for i in range(len(z))])
-    for mode in ("eft", "direct", "ff32"):
+    for mode in ("eft", "direct", "ff32", "wide"):
         cnt, pts = run(A, B, z, mode)
         # degenerate, non-finite and equator cases are exact decisions in every mode
         assert np.array_equal(cnt[:6], want[:6]), (mode, cnt, want)
@@ -155,8 +195,9 @@ def test_edge_cases():
         filled = np.isfinite(pts).all(axis=2).sum(axis=1)
         assert np.array_equal(filled, np.maximum(cnt, 0))
         assert (np.isfinite(pts).all(axis=2) | np.isnan(pts).all(axis=2)).all()
-    cnt, pts = run(A, B, z, "eft")
-    assert np.array_equal(cnt, want)
+    for mode in ("eft", "wide"):
+        cnt, pts = run(A, B, z, mode)
+        assert np.array_equal(cnt, want), mode
 
 
 def test_n_zero_and_bad_arguments():

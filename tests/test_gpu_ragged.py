@@ -110,10 +110,11 @@ def test_small_meshes_equal_all_pairs_reference(ctx, mode, compaction):
     ctx.reset_tuning()
 
 
-def test_small_meshes_against_exact_oracle(ctx):
+@pytest.mark.parametrize("mode", ["eft", "wide"])
+def test_small_meshes_against_exact_oracle(ctx, mode):
     batch = W.ragged_meshes(4, 20, 120, seed=9, lat_min=180, lat_max=260)
     d = to_dev(batch)
-    st, total, recs = run_ragged(ctx, d, "eft")
+    st, total, recs = run_ragged(ctx, d, mode)
     assert st == sphx.OK
     want, flagged, degenerate = oracle_ragged.intersect_ragged(
         batch["A"], batch["B"], batch["edge_offsets"], batch["lat_z"], batch["lat_offsets"])
