@@ -6,7 +6,8 @@
 // shared memory with coalesced 16-byte loads, the per-thread work runs from
 // registers, and the tile's results (kTile x 6 doubles, kTile counts) are
 // staged back through shared memory and written with coalesced 16-byte
-// stores. The grid is a multiple of the SM count and strides over tiles.
+// stores. The grid is one wave of resident blocks (a multiple of the SM count)
+// and strides over the tiles.
 #include "common.cuh"
 #include "intersect.cuh"
 
@@ -89,13 +90,28 @@ static int sm_count_of_current() {
     return sms > 0 ? sms : 1;
 }
 
+// resident blocks per SM of dense_kernel<Mode> (its registers decide)
+template <int Mode>
+static int resident_blocks() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dense_kernel<Mode>, kTile, 0) !=
+            cudaSuccess ||
+        b < 1) {
+        cudaGetLastError();
+        b = 4;
+    }
+    return b;
+}
+
 template <int Mode>
 static void launch_dense(const double *A, const double *B, const double *Z, int64_t n,
                          double *P, int32_t *C, cudaStream_t s) {
-    static int sms = sm_count_of_current();
+    static const int sms = sm_count_of_current();
+    static const int per_sm = resident_blocks<Mode>();
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    // 8 resident 128-thread blocks per SM keep the FP64 pipe fed
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * 8);
+    // exactly one wave of resident blocks: a second, partial wave would leave
+    // most SMs idle while it finishes
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
     dense_kernel<Mode><<<(unsigned)grid, kTile, 0, s>>>(A, B, Z, n, P, C);
 }
 

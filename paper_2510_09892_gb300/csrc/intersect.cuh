@@ -282,7 +282,10 @@ __device__ __forceinline__ void pair_ff32(const double (&x1)[3], const double (&
 // z0 n_x n_z +- s n_y, z0 n_y n_z -+ s n_x and the division by |n_xy|^2 follow
 // with 96-bit mantissas (every numerator term is at most sqrt(1 - z0^2)
 // |n_xy|^2 in magnitude, so 96 bits leave each coordinate within a fraction
-// of an ulp). All of it runs on the 32-bit integer pipe.
+// of an ulp). The square root and the reciprocal start from correctly
+// rounded FP64 values (the only FP64 arithmetic besides the on-arc offsets)
+// refined by one exact correction on the limbs. Everything else runs on the
+// 32-bit integer pipe.
 //
 // On-arc test: t1 = (x1 x P).n = d1 . m1 with m1 = n x x1 and
 // d1 = P - l x1, l = +-1/|x1| (the sign of P . x1): x1 . m1 = 0, so any l
@@ -344,21 +347,24 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
     if (is_zero(n[0]) && is_zero(n[1]) && is_zero(n[2])) return clear(o, -1);
     const bool z0_zero = (bits_of(z0) << 1) == 0;
     if (is_zero(n[0]) && is_zero(n[1])) return clear(o, z0_zero ? -1 : 0);
-    const W<4> S2 = add<4>(mul<4>(n[0], n[0]), mul<4>(n[1], n[1]));
-    const W<4> S3 = add<4>(S2, mul<4>(n[2], n[2]));
+    const W<4> S2 = add_same<4>(sqr<4>(n[0]), sqr<4>(n[1]));
+    const W<4> S3 = add_same<4>(S2, sqr<4>(n[2]));
     const W<2> zz = from_double<2>(z0);
     const W<4> s2 = sub<4>(S2, mul<4>(S3, mul_exact(zz, zz)));
     if (s2.neg && !is_zero(s2)) return clear(o, 0);
     const bool tangent = is_zero(s2);
 
+    // P_xy = g n_xy + sigma h (n_y, -n_x) with g = -z0 n_z / |n_xy|^2 and
+    // h = -s / |n_xy|^2: Eq. 2.2 with the division distributed
     const W<3> nx = narrow<4, 3>(n[0]), ny = narrow<4, 3>(n[1]), nz = narrow<4, 3>(n[2]);
-    const W<3> s = tangent ? zero<3>() : sqrt_pos<3>(narrow<4, 3>(s2));
-    const W<3> rS2 = negate<3>(recip<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
-    const W<3> z3 = from_double<3>(z0);
-    const W<3> zFx = mul<3>(z3, mul<3>(nx, nz));
-    const W<3> zFy = mul<3>(z3, mul<3>(ny, nz));
-    const W<3> sX = mul<3>(s, nx);
-    const W<3> sY = mul<3>(s, ny);
+    const W<3> rS2 = negate<3>(recip_fast<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
+    const W<3> g = mul<3>(mul<3>(from_double<3>(z0), nz), rS2);
+    const W<3> h = tangent ? zero<3>() : mul<3>(sqrt_fast<3>(narrow<4, 3>(s2)), rS2);
+    const W<3> gx = mul<3>(g, nx), gy = mul<3>(g, ny);
+    const W<3> hx = mul<3>(h, nx), hy = mul<3>(h, ny);
+    W<3> Px_lin[2], Py_lin[2];  // both roots: g n_x +- h n_y and g n_y -+ h n_x
+    add_sub<3>(gx, hy, Px_lin[0], Px_lin[1]);
+    add_sub<3>(gy, hx, Py_lin[1], Py_lin[0]);
 
     // on-arc test set-up (FP32 normals and endpoints, scaled by powers of two)
     int emax = n[0].e;
@@ -398,10 +404,8 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
     for (int r = 0; r < 2; ++r) {
         o.hit[r] = false;
         if (r >= nroots) continue;
-        const W<3> X = add<3>(zFx, r == 0 ? sY : negate<3>(sY));
-        const W<3> Y = add<3>(zFy, r == 0 ? negate<3>(sX) : sX);
-        const double Px = to_double<3>(mul<3>(X, rS2));
-        const double Py = to_double<3>(mul<3>(Y, rS2));
+        const double Px = to_double<3>(Px_lin[r]);
+        const double Py = to_double<3>(Py_lin[r]);
         o.px[r] = Px;
         o.py[r] = Py;
         const float pf[3] = {f32_scaled(Px, 0), f32_scaled(Py, 0), zf};

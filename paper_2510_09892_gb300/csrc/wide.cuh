@@ -99,6 +99,88 @@ SPHX_HD float float_of(uint32_t b) {
 #endif
 }
 
+// r = a + b over K limbs; returns the carry out (0 or 1)
+template <int K>
+SPHX_HD uint32_t add_limbs(uint32_t (&r)[K], const uint32_t (&a)[K], const uint32_t (&b)[K]) {
+#if defined(__CUDA_ARCH__)
+    uint32_t c;
+    if (K == 2) {
+        asm("add.cc.u32 %0, %3, %5;\n\taddc.cc.u32 %1, %4, %6;\n\taddc.u32 %2, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+    } else if (K == 3) {
+        asm("add.cc.u32 %0, %4, %7;\n\taddc.cc.u32 %1, %5, %8;\n\taddc.cc.u32 %2, %6, %9;\n\t"
+            "addc.u32 %3, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+    } else {
+        asm("add.cc.u32 %0, %5, %9;\n\taddc.cc.u32 %1, %6, %10;\n\taddc.cc.u32 %2, %7, %11;\n\t"
+            "addc.cc.u32 %3, %8, %12;\n\taddc.u32 %4, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+              "r"(b[3]));
+    }
+    return c;
+#else
+    uint32_t c = 0u;
+    for (int i = 0; i < K; ++i) {
+        const uint64_t t = (uint64_t)a[i] + b[i] + c;
+        r[i] = (uint32_t)t;
+        c = (uint32_t)(t >> 32);
+    }
+    return c;
+#endif
+}
+
+// r = a - b over K limbs; returns the borrow out (0 or 1)
+template <int K>
+SPHX_HD uint32_t sub_limbs(uint32_t (&r)[K], const uint32_t (&a)[K], const uint32_t (&b)[K]) {
+#if defined(__CUDA_ARCH__)
+    uint32_t c;
+    if (K == 2) {
+        asm("sub.cc.u32 %0, %3, %5;\n\tsubc.cc.u32 %1, %4, %6;\n\tsubc.u32 %2, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(b[0]), "r"(b[1]));
+    } else if (K == 3) {
+        asm("sub.cc.u32 %0, %4, %7;\n\tsubc.cc.u32 %1, %5, %8;\n\tsubc.cc.u32 %2, %6, %9;\n\t"
+            "subc.u32 %3, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(b[0]), "r"(b[1]), "r"(b[2]));
+    } else {
+        asm("sub.cc.u32 %0, %5, %9;\n\tsubc.cc.u32 %1, %6, %10;\n\tsubc.cc.u32 %2, %7, %11;\n\t"
+            "subc.cc.u32 %3, %8, %12;\n\tsubc.u32 %4, 0, 0;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(c)
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+              "r"(b[3]));
+    }
+    return c & 1u;
+#else
+    uint32_t bw = 0u;
+    for (int i = 0; i < K; ++i) {
+        const uint64_t t = (uint64_t)a[i] - b[i] - bw;
+        r[i] = (uint32_t)t;
+        bw = (uint32_t)(t >> 63);
+    }
+    return bw;
+#endif
+}
+
+// three-word accumulator (t0, t1, t2) += x * y (product scanning)
+SPHX_HD void mac3(uint32_t &t0, uint32_t &t1, uint32_t &t2, uint32_t x, uint32_t y) {
+#if defined(__CUDA_ARCH__)
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\taddc.u32 %2, %2, 0;"
+        : "+r"(t0), "+r"(t1), "+r"(t2)
+        : "r"(x), "r"(y));
+#else
+    const uint64_t p = (uint64_t)x * y;
+    const uint64_t lo = (uint64_t)t0 + (uint32_t)p;
+    const uint64_t hi = (uint64_t)t1 + (p >> 32) + (lo >> 32);
+    t0 = (uint32_t)lo;
+    t1 = (uint32_t)hi;
+    t2 += (uint32_t)(hi >> 32);
+#endif
+}
+
 template <int K>
 struct W {
     uint32_t m[K];
@@ -153,22 +235,25 @@ SPHX_HD void shr(uint32_t (&m)[K], int d) {
 template <int K>
 SPHX_HD int normalize_mant(uint32_t (&m)[K]) {
     int sh = 0;
+    if (m[K - 1] == 0u) {  // cancellation of 32 bits or more: move whole limbs first
 #pragma unroll
-    for (int step = 0; step < K - 1; ++step) {
-        if (m[K - 1] == 0u) {
+        for (int step = 0; step < K - 1; ++step) {
+            if (m[K - 1] == 0u) {
 #pragma unroll
-            for (int i = K - 1; i > 0; --i) m[i] = m[i - 1];
-            m[0] = 0u;
-            sh += 32;
+                for (int i = K - 1; i > 0; --i) m[i] = m[i - 1];
+                m[0] = 0u;
+                sh += 32;
+            }
         }
+        if (m[K - 1] == 0u) return -1;
     }
-    if (m[K - 1] == 0u) return -1;
     const int c = clz32(m[K - 1]);
 #pragma unroll
     for (int i = K - 1; i > 0; --i) m[i] = funnel_l(m[i - 1], m[i], c);
-    m[0] = c ? (m[0] << c) : m[0];
+    m[0] <<= c;
     return sh + c;
 }
+
 
 template <int K>
 SPHX_HD void normalize(W<K> &a) {
@@ -185,23 +270,21 @@ SPHX_HD void normalize(W<K> &a) {
 template <int K>
 SPHX_HD W<K> from_double(double x) {
     const uint64_t b = bits_of(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    uint64_t frac = b & ((1ull << 52) - 1);
-    W<K> r = zero<K>();
-    if (ex == 0 && frac == 0) return r;
-    r.neg = (uint32_t)(b >> 63);
-    uint64_t t;
-    if (ex == 0) {  // subnormal: value = frac 2^-1074
-        int lz = clz32((uint32_t)(frac >> 32));
-        if (lz == 32) lz += clz32((uint32_t)frac);
-        t = frac << lz;  // top bit set
-        r.e = (64 - lz) - 1074;
-    } else {
-        t = (frac | (1ull << 52)) << 11;
-        r.e = ex - 1022;
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    W<K> r;
+#pragma unroll
+    for (int i = 0; i < K - 2; ++i) r.m[i] = 0u;
+    r.neg = hi >> 31;
+    // normal numbers: the implicit bit and 52 fraction bits, moved to the top
+    r.m[K - 1] = funnel_l(lo, (hi & 0xfffffu) | 0x100000u, 11);
+    r.m[K - 2] = lo << 11;
+    r.e = ex - 1022;
+    if (ex == 0) {  // zero or subnormal (value = fraction 2^-1074)
+        r.m[K - 1] = funnel_l(lo, hi & 0xfffffu, 11);
+        r.e = -1021;
+        normalize<K>(r);
     }
-    r.m[K - 1] = (uint32_t)(t >> 32);
-    r.m[K - 2] = (uint32_t)t;
     return r;
 }
 
@@ -238,67 +321,86 @@ SPHX_HD double to_double(const W<K> &a) {
     return double_of(sign | qq);
 }
 
-// top K limbs of a * b (see the header comment for the truncation)
-template <int K>
-SPHX_HD W<K> mul(const W<K> &a, const W<K> &b) {
-    uint32_t acc[2 * K];
+// product scanning over columns K-1 .. 2K-1 of the 2K-limb product (the
+// lower columns' partial products are dropped, see the header comment);
+// returns the top K limbs normalised, exponent ea + eb (or one less)
+template <int K, bool Square>
+SPHX_HD W<K> mul_scan(const W<K> &a, const W<K> &b) {
+    uint32_t out[K + 1];
+    uint32_t t0 = 0u, t1 = 0u, t2 = 0u;
 #pragma unroll
-    for (int i = 0; i < 2 * K; ++i) acc[i] = 0u;
+    for (int c = K - 1; c < 2 * K; ++c) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        uint32_t carry = 0u;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (i + j >= K - 1) {
-                const uint64_t t = (uint64_t)a.m[i] * b.m[j] + acc[i + j] + carry;
-                acc[i + j] = (uint32_t)t;
-                carry = (uint32_t)(t >> 32);
-            }
+        for (int i = 0; i < K; ++i) {
+            const int j = c - i;
+            if (j < 0 || j >= K) continue;
+            if (Square && i > j) continue;
+            mac3(t0, t1, t2, a.m[i], b.m[j]);
+            if (Square && i < j) mac3(t0, t1, t2, a.m[i], b.m[j]);
         }
-        acc[i + K] = carry;
+        out[c - (K - 1)] = t0;
+        t0 = t1;
+        t1 = t2;
+        t2 = 0u;
     }
     W<K> r;
     r.neg = a.neg ^ b.neg;
     r.e = a.e + b.e;
-    if (is_zero(a) || is_zero(b)) return zero<K>();
-    if (acc[2 * K - 1] >> 31) {
+    if (out[K] >> 31) {
 #pragma unroll
-        for (int i = 0; i < K; ++i) r.m[i] = acc[K + i];
+        for (int i = 0; i < K; ++i) r.m[i] = out[i + 1];
     } else {  // product in [1/4, 1/2): one bit up, taking the guard limb's top bit
 #pragma unroll
-        for (int i = 0; i < K; ++i) r.m[i] = funnel_l(acc[K - 1 + i], acc[K + i], 1);
+        for (int i = 0; i < K; ++i) r.m[i] = funnel_l(out[i], out[i + 1], 1);
         r.e -= 1;
     }
+    if (is_zero(a) || is_zero(b)) return zero<K>();
     return r;
+}
+
+// top K limbs of a * b
+template <int K>
+SPHX_HD W<K> mul(const W<K> &a, const W<K> &b) {
+    return mul_scan<K, false>(a, b);
+}
+
+// top K limbs of a * a (off-diagonal partial products counted twice)
+template <int K>
+SPHX_HD W<K> sqr(const W<K> &a) {
+    return mul_scan<K, true>(a, a);
 }
 
 // exact product of two 2-limb values as a 4-limb value
 SPHX_HD W<4> mul_exact(const W<2> &a, const W<2> &b) {
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        uint32_t carry = 0u;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const uint64_t t = (uint64_t)a.m[i] * b.m[j] + acc[i + j] + carry;
-            acc[i + j] = (uint32_t)t;
-            carry = (uint32_t)(t >> 32);
-        }
-        acc[i + 2] = carry;
-    }
+    uint32_t p[4];
+    uint32_t t0 = 0u, t1 = 0u, t2 = 0u;
+    mac3(t0, t1, t2, a.m[0], b.m[0]);
+    p[0] = t0;
+    t0 = t1;
+    t1 = t2;
+    t2 = 0u;
+    mac3(t0, t1, t2, a.m[0], b.m[1]);
+    mac3(t0, t1, t2, a.m[1], b.m[0]);
+    p[1] = t0;
+    t0 = t1;
+    t1 = t2;
+    t2 = 0u;
+    mac3(t0, t1, t2, a.m[1], b.m[1]);
+    p[2] = t0;
+    p[3] = t1;
     W<4> r;
-    if (is_zero(a) || is_zero(b)) return zero<4>();
     r.neg = a.neg ^ b.neg;
     r.e = a.e + b.e;
-    if (acc[3] >> 31) {
+    if (p[3] >> 31) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) r.m[i] = acc[i];
+        for (int i = 0; i < 4; ++i) r.m[i] = p[i];
     } else {
 #pragma unroll
-        for (int i = 3; i > 0; --i) r.m[i] = funnel_l(acc[i - 1], acc[i], 1);
-        r.m[0] = acc[0] << 1;
+        for (int i = 3; i > 0; --i) r.m[i] = funnel_l(p[i - 1], p[i], 1);
+        r.m[0] = p[0] << 1;
         r.e -= 1;
     }
+    if (is_zero(a) || is_zero(b)) return zero<4>();
     return r;
 }
 
@@ -311,39 +413,49 @@ SPHX_HD W<K> add(W<K> a, W<K> b) {
         b = t;
     }
     shr<K>(b.m, a.e - b.e);
-    const uint32_t sub = a.neg ^ b.neg;
-    const uint32_t mask = 0u - sub;
-    uint32_t carry = sub;
     W<K> r;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        const uint64_t t = (uint64_t)a.m[i] + (b.m[i] ^ mask) + carry;
-        r.m[i] = (uint32_t)t;
-        carry = (uint32_t)(t >> 32);
-    }
     r.e = a.e;
     r.neg = a.neg;
-    if (!sub) {
-        if (carry) {  // overflow into a new top bit
+    if (a.neg == b.neg) {
+        if (add_limbs<K>(r.m, a.m, b.m)) {  // carry into a new top bit
 #pragma unroll
             for (int i = 0; i < K - 1; ++i) r.m[i] = funnel_r(r.m[i], r.m[i + 1], 1);
             r.m[K - 1] = (r.m[K - 1] >> 1) | 0x80000000u;
             r.e += 1;
         }
-        if (is_zero(a)) return b;  // both operands were zero or a was
+        if (is_zero(r)) r.e = kZeroExp;
         return r;
     }
-    if (!carry) {  // |b| > |a|: the difference is negative, take its magnitude
-        uint32_t c = 1u;
+    if (sub_limbs<K>(r.m, a.m, b.m)) {  // |b| > |a| (equal exponents): negate the difference
+        uint32_t z[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const uint64_t t = (uint64_t)(~r.m[i]) + c;
-            r.m[i] = (uint32_t)t;
-            c = (uint32_t)(t >> 32);
-        }
+        for (int i = 0; i < K; ++i) z[i] = 0u;
+        sub_limbs<K>(r.m, z, r.m);
         r.neg ^= 1u;
     }
     normalize<K>(r);
+    return r;
+}
+
+// a + b for operands of the same sign (sums of squares)
+template <int K>
+SPHX_HD W<K> add_same(W<K> a, W<K> b) {
+    if (a.e < b.e) {
+        const W<K> t = a;
+        a = b;
+        b = t;
+    }
+    shr<K>(b.m, a.e - b.e);
+    W<K> r;
+    r.e = a.e;
+    r.neg = a.neg;
+    if (add_limbs<K>(r.m, a.m, b.m)) {
+#pragma unroll
+        for (int i = 0; i < K - 1; ++i) r.m[i] = funnel_r(r.m[i], r.m[i + 1], 1);
+        r.m[K - 1] = (r.m[K - 1] >> 1) | 0x80000000u;
+        r.e += 1;
+    }
+    if (is_zero(r)) r.e = kZeroExp;
     return r;
 }
 
@@ -361,24 +473,6 @@ SPHX_HD W<J> narrow(const W<K> &a) {
     for (int i = 0; i < J; ++i) r.m[i] = a.m[K - J + i];
     r.e = a.e;
     r.neg = a.neg;
-    return r;
-}
-
-// 0.M of a non-zero value as a float (top 24 bits, truncated), in [1/2, 1)
-template <int K>
-SPHX_HD float mant_float(const W<K> &a) {
-    return float_of((126u << 23) | ((a.m[K - 1] >> 8) & 0x7fffffu));
-}
-
-// a small non-negative float as a W<K> (exact)
-template <int K>
-SPHX_HD W<K> from_float(float f) {
-    const uint32_t b = fbits_of(f);
-    W<K> r = zero<K>();
-    if ((b & 0x7fffffffu) == 0u) return r;
-    r.neg = b >> 31;
-    r.e = (int)((b >> 23) & 0xff) - 126;
-    r.m[K - 1] = ((b & 0x7fffffu) | 0x800000u) << 8;
     return r;
 }
 
@@ -407,66 +501,125 @@ SPHX_HD float rsqrt_approx(float x) {
 #endif
 }
 
-SPHX_HD float rsqrt_seed(float x) {
+// correctly rounded FP64 reciprocal and an FP64 reciprocal square root
+// (within a few ulps); the device intrinsics and the host's operations may
+// differ in the last bits of the latter, which the correction step absorbs
+SPHX_HD double rcp_rn(double x) {
 #if defined(__CUDA_ARCH__)
-    return __frsqrt_rn(x);
+    return __drcp_rn(x);
 #else
-    return (float)(1.0 / __builtin_sqrt((double)x));
+    return 1.0 / x;
 #endif
 }
 
-SPHX_HD float rcp_seed(float x) {
+SPHX_HD double rsqrt64(double x) {
 #if defined(__CUDA_ARCH__)
-    return __frcp_rn(x);
+    return rsqrt(x);
 #else
-    return (float)(1.0 / (double)x);
+    return 1.0 / __builtin_sqrt(x);
 #endif
 }
 
-// sqrt(a) for a > 0: Newton's iteration y <- y (3 - f y^2) / 2 for 1/sqrt(f)
-// from a correctly rounded FP32 seed (about 2^-23), twice (about 2^-88),
-// then sqrt(a) = f y 2^h
+// the 96-bit mantissa of a (|a| in [1/4, 2)) as two doubles hi + lo, exactly:
+// hi holds the top 53 bits (truncated), lo the remaining 43
+SPHX_HD void to_dd(const W<3> &a, double &hi, double &lo) {
+    const uint64_t t = ((uint64_t)a.m[2] << 32) | a.m[1];
+    const uint64_t sign = (uint64_t)a.neg << 63;
+    hi = double_of(sign | ((uint64_t)(a.e + 1022) << 52) | ((t >> 11) & ((1ull << 52) - 1)));
+    const uint64_t R = ((uint64_t)(a.m[1] & 0x7ffu) << 32) | a.m[0];
+    if (R == 0) {
+        lo = 0.0;
+        return;
+    }
+    int lz = clz32((uint32_t)(R >> 32));
+    if (lz == 32) lz += clz32((uint32_t)R);
+    const int bl = 64 - lz;  // R = 0.R' 2^bl
+    lo = double_of(sign | ((uint64_t)(a.e - 96 + bl + 1022) << 52) |
+                   ((R << (53 - bl)) & ((1ull << 52) - 1)));
+}
+
+// hi + lo (|lo| well below |hi|) as a W<K>
 template <int K>
-SPHX_HD W<K> sqrt_pos(const W<K> &a) {
-    // a = f 2^(2h): f = 0.M in [1/2, 1) for an even exponent, 0.M / 2 in
-    // [1/4, 1/2) for an odd one
-    W<K> f = a;
+SPHX_HD W<K> from_dd(double hi, double lo) {
+    return add<K>(from_double<K>(hi), from_double<K>(lo));
+}
+
+// sqrt(a) for a > 0 to about 2^-100: with a = f 2^(2h), f = fh + fl in
+// [1/4, 1), d = fh y for y ~ 1/sqrt(fh) is within a few ulps of sqrt(f), and
+// one Newton step sqrt(f) = d + (f - d^2) y / 2 + O(2^-100) has its residual
+// f - d^2 = fma(-d, d, fh) + fl correct to about 2^-104
+template <int K>
+SPHX_HD W<K> sqrt_fast(const W<K> &a) {
+    static_assert(K == 3, "sqrt_fast works on 96-bit mantissas");
+    W<3> f = a;
     const int odd = a.e & 1;
     f.e = -odd;
     f.neg = 0u;
     const int h = (a.e + odd) / 2;
-    float ff = mant_float<K>(a);
-    if (odd) ff *= 0.5f;
-    W<K> y = from_float<K>(rsqrt_seed(ff));
-    W<K> three = zero<K>();
-    three.m[K - 1] = 0xC0000000u;  // 0.75 * 2^2
-    three.e = 2;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        W<K> t = mul<K>(f, mul<K>(y, y));
-        y = mul<K>(y, sub<K>(three, t));
-        y.e -= 1;
-    }
-    W<K> s = mul<K>(f, y);
+    double fh, fl;
+    to_dd(f, fh, fl);
+    const double y = rsqrt64(fh);
+    const double d = fh * y;
+    const double res = fma64(-d, d, fh) + fl;
+    W<3> s = from_dd<3>(d, res * (0.5 * y));
     s.e += h;
     return s;
 }
 
-// 1 / a for a != 0: Newton's iteration r <- r (2 - f r) from an FP32 seed, twice
+// 1 / a for a != 0 to about 2^-100: with f = fh + fl the mantissa of a in
+// [1/2, 1) and r = RN(1 / fh), 1 - fh r is exact by one FMA and
+// 1 / f = r (1 + e) + O(2^-104), e = (1 - fh r) - fl r
 template <int K>
-SPHX_HD W<K> recip(const W<K> &a) {
-    W<K> f = a;
+SPHX_HD W<K> recip_fast(const W<K> &a) {
+    static_assert(K == 3, "recip_fast works on 96-bit mantissas");
+    W<3> f = a;
     f.e = 0;
     f.neg = 0u;
-    W<K> r = from_float<K>(rcp_seed(mant_float<K>(a)));
-    W<K> two = zero<K>();
-    two.m[K - 1] = 0x80000000u;  // 0.5 * 2^2
-    two.e = 2;
+    double fh, fl;
+    to_dd(f, fh, fl);
+    const double r = rcp_rn(fh);
+    const double e = fma64(-fl, r, fma64(-fh, r, 1.0));
+    W<3> q = from_dd<3>(r, r * e);
+    q.e -= a.e;
+    q.neg = a.neg;
+    return q;
+}
+
+// s = a + b and d = a - b, sharing the alignment
+template <int K>
+SPHX_HD void add_sub(W<K> a, W<K> b, W<K> &s, W<K> &d) {
+    const bool sw = a.e < b.e;
+    if (sw) {
+        const W<K> t = a;
+        a = b;
+        b = t;
+    }
+    shr<K>(b.m, a.e - b.e);
+    W<K> ad, sb;  // magnitude sum and difference, signed like a
+    ad.e = sb.e = a.e;
+    ad.neg = sb.neg = a.neg;
+    if (add_limbs<K>(ad.m, a.m, b.m)) {
 #pragma unroll
-    for (int it = 0; it < 2; ++it) r = mul<K>(r, sub<K>(two, mul<K>(f, r)));
-    r.e -= a.e;
-    r.neg = a.neg;
-    return r;
+        for (int i = 0; i < K - 1; ++i) ad.m[i] = funnel_r(ad.m[i], ad.m[i + 1], 1);
+        ad.m[K - 1] = (ad.m[K - 1] >> 1) | 0x80000000u;
+        ad.e += 1;
+    }
+    if (is_zero(ad)) ad.e = kZeroExp;
+    if (sub_limbs<K>(sb.m, a.m, b.m)) {
+        uint32_t z[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) z[i] = 0u;
+        sub_limbs<K>(sb.m, z, sb.m);
+        sb.neg ^= 1u;
+    }
+    normalize<K>(sb);
+    // a + b is the magnitude sum when the signs agree, else the difference;
+    // a - b the other one (negated back when the operands were swapped)
+    const bool same = a.neg == b.neg;
+    s = same ? ad : sb;
+    d = same ? sb : ad;
+    if (sw) d.neg ^= 1u;
+    if (is_zero(d)) d.neg = 0u;
 }
 
 }  // namespace wide
