@@ -397,7 +397,6 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
     const double inv1 = unit1 ? 1.0 : f64_of_f32_scaled(r1, sc1);
     const double inv2 = unit2 ? 1.0 : f64_of_f32_scaled(r2, sc2);
     const float zf = f32_scaled(z0, 0);
-
     const int nroots = tangent ? 1 : 2;
     o.count = 0;
 #pragma unroll
@@ -411,9 +410,11 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
         const float pf[3] = {f32_scaled(Px, 0), f32_scaled(Py, 0), zf};
         const double l1 = (pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f) ? inv1 : -inv1;
         const double l2 = (pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f) ? inv2 : -inv2;
-        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0), f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
+        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0),
+                             f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
                              f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
-        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0), f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
+        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0),
+                             f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
                              f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
         const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
         const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));

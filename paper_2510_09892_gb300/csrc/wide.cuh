@@ -501,23 +501,38 @@ SPHX_HD float rsqrt_approx(float x) {
 #endif
 }
 
-// correctly rounded FP64 reciprocal and an FP64 reciprocal square root
-// (within a few ulps); the device intrinsics and the host's operations may
-// differ in the last bits of the latter, which the correction step absorbs
-SPHX_HD double rcp_rn(double x) {
+// correctly rounded FP32 reciprocal and reciprocal square root (about 2^-24),
+// the seeds of the FP64 steps below; the host computes the same roundings
+SPHX_HD float rcp32(float x) {
 #if defined(__CUDA_ARCH__)
-    return __drcp_rn(x);
+    return __frcp_rn(x);
 #else
-    return 1.0 / x;
+    return (float)(1.0 / (double)x);
 #endif
 }
 
-SPHX_HD double rsqrt64(double x) {
+SPHX_HD float rsqrt32(float x) {
 #if defined(__CUDA_ARCH__)
-    return rsqrt(x);
+    return __frsqrt_rn(x);
 #else
-    return 1.0 / __builtin_sqrt(x);
+    return (float)(1.0 / __builtin_sqrt((double)x));
 #endif
+}
+
+// a double in [2^-126, 2^127) as a float (mantissa truncated), by its bits
+SPHX_HD float f32_of_f64(double x) {
+    const uint64_t b = bits_of(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const uint32_t fe = ((hi >> 20) & 0x7ffu) - 1023u + 127u;
+    return float_of((hi & 0x80000000u) | (fe << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
+// a normal float as a double (exact), by its bits
+SPHX_HD double f64_of_f32(float f) {
+    const uint32_t b = fbits_of(f);
+    const uint64_t fe = ((b >> 23) & 0xffu) - 127u + 1023u;
+    return double_of(((uint64_t)(b & 0x80000000u) << 32) | (fe << 52) |
+                     ((uint64_t)(b & 0x7fffffu) << 29));
 }
 
 // the 96-bit mantissa of a (|a| in [1/4, 2)) as two doubles hi + lo, exactly:
@@ -544,10 +559,10 @@ SPHX_HD W<K> from_dd(double hi, double lo) {
     return add<K>(from_double<K>(hi), from_double<K>(lo));
 }
 
-// sqrt(a) for a > 0 to about 2^-100: with a = f 2^(2h), f = fh + fl in
-// [1/4, 1), d = fh y for y ~ 1/sqrt(fh) is within a few ulps of sqrt(f), and
-// one Newton step sqrt(f) = d + (f - d^2) y / 2 + O(2^-100) has its residual
-// f - d^2 = fma(-d, d, fh) + fl correct to about 2^-104
+// sqrt(a) for a > 0 to about 2^-90: with a = f 2^(2h), f = fh + fl in
+// [1/4, 1): an FP32 seed y0 ~ 1/sqrt(fh) (2^-24), one FP64 Newton step
+// y = y0 + y0 (1 - fh y0^2) / 2 (2^-46), d = fh y, then one exact-residual
+// step sqrt(f) = d + (f - d^2) y / 2, with f - d^2 = fma(-d, d, fh) + fl
 template <int K>
 SPHX_HD W<K> sqrt_fast(const W<K> &a) {
     static_assert(K == 3, "sqrt_fast works on 96-bit mantissas");
@@ -558,7 +573,8 @@ SPHX_HD W<K> sqrt_fast(const W<K> &a) {
     const int h = (a.e + odd) / 2;
     double fh, fl;
     to_dd(f, fh, fl);
-    const double y = rsqrt64(fh);
+    const double y0 = f64_of_f32(rsqrt32(f32_of_f64(fh)));
+    const double y = fma64(0.5 * y0, fma64(-fh * y0, y0, 1.0), y0);
     const double d = fh * y;
     const double res = fma64(-d, d, fh) + fl;
     W<3> s = from_dd<3>(d, res * (0.5 * y));
@@ -566,9 +582,9 @@ SPHX_HD W<K> sqrt_fast(const W<K> &a) {
     return s;
 }
 
-// 1 / a for a != 0 to about 2^-100: with f = fh + fl the mantissa of a in
-// [1/2, 1) and r = RN(1 / fh), 1 - fh r is exact by one FMA and
-// 1 / f = r (1 + e) + O(2^-104), e = (1 - fh r) - fl r
+// 1 / a for a != 0 to about 2^-90: with f = fh + fl the mantissa of a in
+// [1/2, 1): an FP32 seed r0 ~ 1 / fh, one FP64 Newton step r = r0 + r0 (1 - fh r0)
+// (2^-46), then 1 / f = r (1 + e) + O(e^2) with e = (1 - fh r) - fl r
 template <int K>
 SPHX_HD W<K> recip_fast(const W<K> &a) {
     static_assert(K == 3, "recip_fast works on 96-bit mantissas");
@@ -577,7 +593,8 @@ SPHX_HD W<K> recip_fast(const W<K> &a) {
     f.neg = 0u;
     double fh, fl;
     to_dd(f, fh, fl);
-    const double r = rcp_rn(fh);
+    const double r0 = f64_of_f32(rcp32(f32_of_f64(fh)));
+    const double r = fma64(r0, fma64(-fh, r0, 1.0), r0);
     const double e = fma64(-fl, r, fma64(-fh, r, 1.0));
     W<3> q = from_dd<3>(r, r * e);
     q.e -= a.e;
