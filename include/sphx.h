@@ -154,6 +154,38 @@ sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const doub
                                   sphx_mode mode, sphx_hit *out, int64_t out_cap,
                                   int64_t *out_total, sphx_stream stream);
 
+/* Largest edge count sphx_intersect_ragged_noalloc accepts. */
+#define SPHX_NOALLOC_MAX_EDGES 262144
+
+/* The ragged call for callers that must not allocate device memory on their
+   call path. The paper has no counterpart: this is a property of the library,
+   not of the method. Examples are plugins whose host framework owns the
+   device memory budget (a cudaMalloc behind its back can fail, or break that
+   framework's accounting) and latency-critical loops that cannot afford
+   cudaMalloc's implicit device synchronisation.
+   Arguments and results are those of sphx_intersect_ragged. There is no
+   context and no caller-given ranges (they are always computed). Output
+   order is unspecified (unordered compaction).
+   Scratch: a fixed device array of about 4.2 MB inside this library, holding
+   room for SPHX_NOALLOC_MAX_EDGES edges. Every GPU that loads the library
+   holds it until the process exits.
+   E > SPHX_NOALLOC_MAX_EDGES returns SPHX_ERR_INVALID_ARG and launches
+   nothing. Nothing is allocated: no cudaMalloc, no cudaFree, no allocating
+   library routine.
+   The first call on a device looks up the array's device address (with that
+   device current). Make that first call before any stream capture.
+   All calls share the one array. The counters that must start at zero are
+   cleared by each call, on its stream. Calls that overlap on the GPU (other
+   streams, other host threads) race on the array and must be serialised by
+   the caller.
+   A capacity overflow shows as *out_total > out_cap (only out_cap records
+   are written). */
+sphx_status sphx_intersect_ragged_noalloc(const double *A, const double *B,
+                                          const int64_t *edge_offsets, int32_t M, int64_t E,
+                                          const double *lat_z, const int64_t *lat_offsets,
+                                          int64_t L, sphx_mode mode, sphx_hit *out,
+                                          int64_t out_cap, int64_t *out_total, sphx_stream stream);
+
 /* Synchronise `stream`, read and clear the context's device status word.
    Returns SPHX_OK, SPHX_ERR_CAPACITY or SPHX_ERR_TIMEOUT (or SPHX_ERR_CUDA). */
 sphx_status sphx_sync_status(sphx_context *ctx, sphx_stream stream);

@@ -57,6 +57,8 @@ _SIGS = {
     "sphx_candidate_ranges": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "sphx_intersect_ragged": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp,
                                              ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "sphx_intersect_ragged_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64,
+                                                     ctypes.c_int, _vp, _i64, _vp, _vp]),
     "sphx_sync_status": (ctypes.c_int, [_vp, _vp]),
     "sphx_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     "sphx_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
@@ -240,6 +242,28 @@ def sphx_intersect_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, 
                                      _ptr(edge_lat_hi), _mode(mode), _ptr(out), cap,
                                      _ptr(out_total), _stream(stream))
     _check(st, "sphx_intersect_ragged")
+
+
+NOALLOC_MAX_EDGES = 262144
+
+
+def sphx_intersect_ragged_noalloc(A, B, edge_offsets, lat_z, lat_offsets, out, out_total,
+                                  mode="eft", stream=None):
+    """The ragged call on the library's fixed scratch array (no allocation).
+
+    Same arguments and results as sphx_intersect_ragged, without a context or
+    caller-given ranges; E may not exceed NOALLOC_MAX_EDGES. A capacity
+    overflow shows as out_total > capacity. Calls that overlap on the GPU race
+    on the shared scratch and must be serialised by the caller.
+    """
+    M = int(edge_offsets.shape[0]) - 1
+    E = int(A.shape[0])
+    L = int(lat_z.shape[0])
+    cap = out.numel() * out.element_size() // HIT_BYTES
+    st = lib().sphx_intersect_ragged_noalloc(_ptr(A), _ptr(B), _ptr(edge_offsets), M, E,
+                                             _ptr(lat_z), _ptr(lat_offsets), L, _mode(mode),
+                                             _ptr(out), cap, _ptr(out_total), _stream(stream))
+    _check(st, "sphx_intersect_ragged_noalloc")
 
 
 def sphx_autotune_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, out, out_total,
