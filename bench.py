@@ -363,63 +363,35 @@ def cpu_baseline_leg() -> dict:
 
 
 def e2e_leg(sphx, torch, dev, A, B, z, args, mode) -> dict:
-    """Same metric through the C ABI from pinned HOST buffers: every step copies
-    the inputs in and the points and counts out, in 4 chunks over 2 streams so
-    the copies overlap the kernels."""
+    """Same metric through the C ABI from pinned HOST buffers
+    (sphx_intersect_gca_constlat_host): every step copies the inputs in and the
+    points and counts out, pipelined with the kernels inside the library."""
     n = len(z)
     hA = torch.from_numpy(A).pin_memory()
     hB = torch.from_numpy(B).pin_memory()
     hz = torch.from_numpy(z).pin_memory()
     hP = torch.empty((n, 2, 3), dtype=torch.float64).pin_memory()
     hC = torch.empty((n,), dtype=torch.int32).pin_memory()
-    chunks = 4
-    step = (n + chunks - 1) // chunks
-    step = (step + 127) // 128 * 128
-    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
-    bufs = []
-    for i in range(2):
-        bufs.append((torch.empty((step, 3), dtype=torch.float64, device=dev),
-                     torch.empty((step, 3), dtype=torch.float64, device=dev),
-                     torch.empty((step,), dtype=torch.float64, device=dev),
-                     torch.empty((step, 2, 3), dtype=torch.float64, device=dev),
-                     torch.empty((step,), dtype=torch.int32, device=dev)))
-
-    def one_step():
-        for c in range(chunks):
-            lo, hi = c * step, min(n, (c + 1) * step)
-            if lo >= hi:
-                break
-            m = hi - lo
-            s = streams[c % 2]
-            dA, dB, dz, dP, dC = bufs[c % 2]
-            with torch.cuda.stream(s):
-                dA[:m].copy_(hA[lo:hi], non_blocking=True)
-                dB[:m].copy_(hB[lo:hi], non_blocking=True)
-                dz[:m].copy_(hz[lo:hi], non_blocking=True)
-                sphx.sphx_intersect_gca_constlat(dA[:m], dB[:m], dz[:m], dP[:m], dC[:m], mode, s)
-                hP[lo:hi].copy_(dP[:m], non_blocking=True)
-                hC[lo:hi].copy_(dC[:m], non_blocking=True)
-
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     cur = torch.cuda.current_stream(dev)
-    e0.record(cur)
-    for s in streams:
-        s.wait_stream(cur)
-    for _ in range(args.steps):
-        one_step()
-    for s in streams:
-        cur.wait_stream(s)
-    e1.record(cur)
-    torch.cuda.synchronize()
+    with sphx.Context(dev.index or 0) as ctx:
+        for _ in range(args.warmup):
+            sphx.sphx_intersect_gca_constlat_host(ctx, hA, hB, hz, hP, hC, mode, cur)
+        sphx.sphx_host_join(ctx, cur)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(args.steps):
+            sphx.sphx_intersect_gca_constlat_host(ctx, hA, hB, hz, hP, hC, mode, cur)
+        sphx.sphx_host_join(ctx, cur)  # every step's results are back in host memory
+        e1.record(cur)
+        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_max(ms, dev)
     _, world, _ = dist_env()
     return {"value": world * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "h2d_bytes_per_step": n * 56, "d2h_bytes_per_step": n * 52}
+            "h2d_bytes_per_step": n * 56, "d2h_bytes_per_step": n * 52,
+            "path": "sphx_intersect_gca_constlat_host, pinned host buffers"}
 
 
 if __name__ == "__main__":

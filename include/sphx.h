@@ -121,6 +121,30 @@ sphx_status sphx_intersect_gca_constlat(const double *A, const double *B, const 
                                         int64_t n, double *out_pts, int32_t *out_count,
                                         sphx_mode mode, sphx_stream stream);
 
+/* Dense call on HOST buffers (same problem and layouts as
+   sphx_intersect_gca_constlat; A, B, z0, out_pts, out_count are host
+   pointers, best page-locked). The arcs go through the context's device
+   staging in three chunks (of at most 524288 arcs; more chunks beyond that),
+   each on its own stream of the context, so that the copies in both
+   directions overlap the kernels. The staging (156 B per arc of a chunk, per
+   stream) is allocated when a call needs more than the last and kept.
+   The work starts after the work already enqueued on `stream` but does not
+   hold `stream` back: successive calls on one context overlap (one call's
+   results going out while the next call's inputs come in). The host outputs
+   are complete once sphx_host_join(ctx, stream) has been enqueued and
+   `stream` has synchronised. Returns after enqueuing. The host buffers must
+   stay valid until then. Calls on one context must come from one host thread
+   at a time. */
+sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A, const double *B,
+                                             const double *z0, int64_t n, double *out_pts,
+                                             int32_t *out_count, sphx_mode mode,
+                                             sphx_stream stream);
+
+/* Make `stream` wait for every sphx_intersect_gca_constlat_host call
+   enqueued on `ctx` so far (their copies out included). Returns after
+   enqueuing. */
+sphx_status sphx_host_join(sphx_context *ctx, sphx_stream stream);
+
 /* Candidate latitude ranges of a ragged batch (step a11 of the hot path):
    for each edge e of mesh m, [lo[e], hi[e]) indexes lat_z (global indices)
    and covers every latitude of mesh m inside the edge's z-range (the endpoint

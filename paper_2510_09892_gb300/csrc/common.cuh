@@ -81,6 +81,22 @@ cudaError_t launch_scan(const int32_t *lo, const int32_t *hi, int64_t E, long lo
 cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, int sm_count,
                           cudaStream_t s);
 
+// device staging of the host-buffer dense call: kHostSlots chunks in flight,
+// one stream each (copy in, kernel, copy out stay in order on a slot's
+// stream). Each copy costs several microseconds of set-up, so the arcs go in
+// as few chunks as keep both copy directions and the kernels overlapped: one
+// per slot, up to kHostMaxChunk arcs each.
+constexpr int kHostSlots = 3;
+constexpr int64_t kHostMaxChunk = int64_t(1) << 19;  // arcs per chunk, at most
+struct HostStaging {
+    int64_t cap = 0;  // arcs per slot the buffers hold
+    double *A[kHostSlots] = {}, *B[kHostSlots] = {}, *z[kHostSlots] = {}, *P[kHostSlots] = {};
+    int32_t *C[kHostSlots] = {};
+    cudaStream_t s[kHostSlots] = {};
+    cudaEvent_t done[kHostSlots] = {};
+    cudaEvent_t start = nullptr;
+};
+
 struct GraphKey {
     std::vector<uintptr_t> v;
     bool operator<(const GraphKey &o) const { return v < o.v; }
@@ -97,5 +113,6 @@ struct sphx_context {
     bool tuned = false;          // tuning fixed by sphx_set_tuning / autotune
     sphx::RaggedShape shape;
     std::map<sphx::GraphKey, cudaGraphExec_t> graphs;
+    sphx::HostStaging host;
     std::mutex mu;
 };

@@ -41,6 +41,47 @@ void free_scratch(RaggedScratch &s) {
     s = RaggedScratch();
 }
 
+void free_host_staging(HostStaging &h) {
+    for (int i = 0; i < kHostSlots; ++i) {
+        cudaFree(h.A[i]);
+        cudaFree(h.B[i]);
+        cudaFree(h.z[i]);
+        cudaFree(h.P[i]);
+        cudaFree(h.C[i]);
+        if (h.s[i]) cudaStreamDestroy(h.s[i]);
+        if (h.done[i]) cudaEventDestroy(h.done[i]);
+    }
+    if (h.start) cudaEventDestroy(h.start);
+    h = HostStaging();
+}
+
+sphx_status ensure_host_staging(sphx_context *ctx, int64_t chunk, cudaStream_t us) {
+    HostStaging &h = ctx->host;
+    if (h.cap >= chunk) return SPHX_OK;
+    // growing: the old buffers may still be in use by earlier calls
+    if (h.cap > 0) SPHX_CUDA(cudaStreamSynchronize(us));
+    for (int i = 0; i < kHostSlots; ++i)
+        if (h.s[i]) SPHX_CUDA(cudaStreamSynchronize(h.s[i]));
+    free_host_staging(h);
+    bool ok = cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < kHostSlots; ++i) {
+        ok = cudaMalloc(&h.A[i], chunk * 3 * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&h.B[i], chunk * 3 * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&h.z[i], chunk * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&h.P[i], chunk * 6 * sizeof(double)) == cudaSuccess &&
+             cudaMalloc(&h.C[i], chunk * sizeof(int32_t)) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&h.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h.done[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_host_staging(h);
+        return SPHX_ERR_NOMEM;
+    }
+    h.cap = chunk;
+    return SPHX_OK;
+}
+
 void drop_graphs(sphx_context *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
@@ -320,6 +361,7 @@ void sphx_destroy(sphx_context *ctx) {
     cudaDeviceSynchronize();
     drop_graphs(ctx);
     free_scratch(ctx->scratch);
+    free_host_staging(ctx->host);
     cudaFree(ctx->status);
     cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
@@ -338,6 +380,56 @@ sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const doub
     if (st != SPHX_OK) return st;
     std::lock_guard<std::mutex> g(ctx->mu);
     return run_ragged(ctx, c, effective_shape(ctx), reinterpret_cast<cudaStream_t>(stream));
+}
+
+sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A, const double *B,
+                                             const double *z0, int64_t n, double *out_pts,
+                                             int32_t *out_count, sphx_mode mode,
+                                             sphx_stream stream) {
+    if (!ctx || n < 0) return SPHX_ERR_INVALID_ARG;
+    if (n == 0) return SPHX_OK;
+    if (!A || !B || !z0 || !out_pts || !out_count) return SPHX_ERR_INVALID_ARG;
+    if ((int)mode < 0 || (int)mode > 4) return SPHX_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+    int64_t chunk = (n + kHostSlots - 1) / kHostSlots;
+    chunk = std::min<int64_t>(kHostMaxChunk, (chunk + 127) / 128 * 128);
+    sphx_status st = ensure_host_staging(ctx, chunk, us);
+    if (st != SPHX_OK) return st;
+    HostStaging &h = ctx->host;
+    // every slot stream starts after the work already on the caller's stream
+    SPHX_CUDA(cudaEventRecord(h.start, us));
+    for (int i = 0; i < kHostSlots; ++i) SPHX_CUDA(cudaStreamWaitEvent(h.s[i], h.start, 0));
+    const int64_t chunks = (n + chunk - 1) / chunk;
+    for (int64_t c = 0; c < chunks; ++c) {
+        const int i = (int)(c % kHostSlots);
+        const int64_t lo = c * chunk, m = std::min<int64_t>(chunk, n - lo);
+        cudaStream_t s = h.s[i];
+        // copy in, compute, copy out: in order on the slot's stream, so a slot's
+        // buffers are reused only after its previous chunk has been copied out
+        SPHX_CUDA(cudaMemcpyAsync(h.A[i], A + 3 * lo, m * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+        SPHX_CUDA(cudaMemcpyAsync(h.B[i], B + 3 * lo, m * 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+        SPHX_CUDA(cudaMemcpyAsync(h.z[i], z0 + lo, m * sizeof(double), cudaMemcpyHostToDevice, s));
+        st = sphx_intersect_gca_constlat(h.A[i], h.B[i], h.z[i], m, h.P[i], h.C[i], mode,
+                                         reinterpret_cast<sphx_stream>(s));
+        if (st != SPHX_OK) return st;
+        SPHX_CUDA(cudaMemcpyAsync(out_pts + 6 * lo, h.P[i], m * 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SPHX_CUDA(cudaMemcpyAsync(out_count + lo, h.C[i], m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
+    return SPHX_OK;
+}
+
+sphx_status sphx_host_join(sphx_context *ctx, sphx_stream stream) {
+    if (!ctx) return SPHX_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    HostStaging &h = ctx->host;
+    if (h.cap == 0) return SPHX_OK;
+    cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < kHostSlots; ++i) {
+        SPHX_CUDA(cudaEventRecord(h.done[i], h.s[i]));
+        SPHX_CUDA(cudaStreamWaitEvent(us, h.done[i], 0));
+    }
+    return SPHX_OK;
 }
 
 sphx_status sphx_sync_status(sphx_context *ctx, sphx_stream stream) {

@@ -54,6 +54,9 @@ _SIGS = {
     "sphx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
     "sphx_destroy": (None, [_vp]),
     "sphx_intersect_gca_constlat": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
+    "sphx_intersect_gca_constlat_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp,
+                                                        ctypes.c_int, _vp]),
+    "sphx_host_join": (ctypes.c_int, [_vp, _vp]),
     "sphx_candidate_ranges": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "sphx_intersect_ragged": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp,
                                              ctypes.c_int, _vp, _i64, _vp, _vp]),
@@ -212,6 +215,36 @@ class Context:
 
     def sync_status(self, stream=None) -> int:
         return lib().sphx_sync_status(self.handle, _stream(stream))
+
+
+def _host_tensor(t, dtype, name, shape):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+
+
+def sphx_intersect_gca_constlat_host(ctx: "Context", A, B, z0, out_pts, out_count, mode="wide",
+                                     stream=None):
+    """Dense call on host tensors (best pinned): copies in, kernels and copies
+    out pipelined on the context's streams, ordered after the work already on
+    `stream` (default: the current stream). The outputs are complete after
+    sphx_host_join(ctx, stream) and a synchronisation of `stream`."""
+    n = int(z0.shape[0])
+    _host_tensor(A, torch.float64, "A", (n, 3))
+    _host_tensor(B, torch.float64, "B", (n, 3))
+    _host_tensor(z0, torch.float64, "z0", (n,))
+    _host_tensor(out_pts, torch.float64, "out_pts", (n, 2, 3))
+    _host_tensor(out_count, torch.int32, "out_count", (n,))
+    st = lib().sphx_intersect_gca_constlat_host(ctx.handle, _ptr(A), _ptr(B), _ptr(z0), n,
+                                                _ptr(out_pts), _ptr(out_count), _mode(mode),
+                                                _stream(stream))
+    _check(st, "sphx_intersect_gca_constlat_host")
+
+
+def sphx_host_join(ctx: "Context", stream=None):
+    """Make `stream` wait for every host-buffer call enqueued on ctx so far."""
+    _check(lib().sphx_host_join(ctx.handle, _stream(stream)), "sphx_host_join")
 
 
 def sphx_candidate_ranges(A, B, edge_offsets, lat_z, lat_offsets, lo, hi, stream=None):

@@ -258,3 +258,47 @@ def test_full_size_stress_workload_sampled():
     cd, pd = run(A, B, z, "direct")
     cr, pr = steps.direct(A, B, z)
     assert np.array_equal(cd, cr) and P.same_bits(pd, pr)
+
+
+@pytest.mark.parametrize("n", [1, 1_000, 393_217, 1_572_865])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_call_equals_device_call(n, pinned):
+    """sphx_intersect_gca_constlat_host: three chunks (more past 3 x 2^19 arcs)
+    through the context's staging; identical results to the device-buffer
+    call, including uneven chunks and pageable host memory."""
+    A, B, z = W.stress_arcs(n, seed=50 + n % 7)
+    cnt_d, pts_d = run(A, B, z, "wide")
+    hA, hB, hz = (torch.from_numpy(np.ascontiguousarray(v)) for v in (A, B, z))
+    hP = torch.full((n, 2, 3), 5.0, dtype=torch.float64)
+    hC = torch.full((n,), -9, dtype=torch.int32)
+    if pinned:
+        hA, hB, hz, hP, hC = (t.pin_memory() for t in (hA, hB, hz, hP, hC))
+    with sphx.Context(0) as ctx:
+        for _ in range(2):  # the second call reuses the staging
+            sphx.sphx_intersect_gca_constlat_host(ctx, hA, hB, hz, hP, hC, "wide")
+            sphx.sphx_host_join(ctx)
+            torch.cuda.synchronize()
+            assert np.array_equal(hC.numpy(), cnt_d)
+            assert P.same_bits(hP.numpy(), pts_d)
+            hP.fill_(5.0)
+            hC.fill_(-9)
+
+
+def test_host_buffer_calls_overlap_and_join():
+    """Successive host-buffer calls on one context, different batches, one
+    join at the end: every call's outputs are complete and correct."""
+    batches = [W.uniform_arcs(200_003, seed=60 + k) for k in range(3)]
+    want = [run(A, B, z, "wide") for A, B, z in batches]
+    outs = []
+    with sphx.Context(0) as ctx:
+        for A, B, z in batches:
+            hA, hB, hz = (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in (A, B, z))
+            hP = torch.empty((len(z), 2, 3), dtype=torch.float64).pin_memory()
+            hC = torch.empty(len(z), dtype=torch.int32).pin_memory()
+            sphx.sphx_intersect_gca_constlat_host(ctx, hA, hB, hz, hP, hC, "wide")
+            outs.append((hA, hB, hz, hP, hC))
+        sphx.sphx_host_join(ctx)
+        torch.cuda.synchronize()
+    for (cnt, pts), (_, _, _, hP, hC) in zip(want, outs):
+        assert np.array_equal(hC.numpy(), cnt)
+        assert P.same_bits(hP.numpy(), pts)
