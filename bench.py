@@ -45,7 +45,11 @@ WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-uniform 
 # algorithmic work per arc of the dense call (both roots and the on-arc test)
 BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
-INT_OPS_PER_ARC = {}  # 32-bit integer operations per arc of the integer-limb kernel
+# thread instructions per arc of dense_kernel<WIDE> (ncu smsp__inst_executed.sum x 32
+# / arcs on the 10^6-arc stress workload): the integer-limb method's work per arc
+INST_PER_ARC = {"wide": 2560}
+ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
+SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
           "direct": "f64", "ff32": "f32 pairs + f64"}
 L2_FLUSH_BYTES = 256 << 20
@@ -203,6 +207,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sphx", choices=["sphx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the ragged (regridding) leg reported beside the headline")
     ap.add_argument("--mode", default="wide", choices=["wide", "eft", "direct", "ff32"],
                     help="headline evaluation mode (the others are timed beside it)")
     args = ap.parse_args()
@@ -249,6 +255,7 @@ def main():
         stream.synchronize()
         return [a.elapsed_time(b) for a, b in ms]
 
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     fp64_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP64) / 2  # FMA/s = FP64 op slots/s
     fp32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP32) / 2
     int32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_INT32)
@@ -285,6 +292,8 @@ def main():
     clk = clocks.summary()
     clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
 
+    ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
+
     # hits per step, from one more headline call's outputs
     sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, head)
     hits = int(torch.clamp(cnt, min=0).sum().item())
@@ -300,15 +309,19 @@ def main():
 
     def alu_roof(ms, ops_per_arc, peak, pipe):
         rate = ops_per_arc * N_ARCS / (ms * 1e-3)
+        measured = "issue" not in pipe
         return {"bound": "alu", "unit": "Tops/s", "achieved": rate / 1e12, "peak": peak / 1e12,
                 "frac": rate / peak, "traffic": None,
-                "note": f"{pipe}: {ops_per_arc} operations per arc against the pipe's issue "
-                        "rate measured live by sphx_probe_fma_rate (of measured)"}
+                "note": f"{pipe}: {ops_per_arc} operations per arc against "
+                        + ("the pipe's rate measured live by sphx_probe_fma_rate (of measured)"
+                           if measured else
+                           "4 x 32 lanes x SMs x the 2070 MHz maximum SM clock (derived)")}
 
     head_kernel_ms = statistics.mean(head_ms)
-    if head in INT_OPS_PER_ARC:
-        roofline = alu_roof(head_kernel_ms, INT_OPS_PER_ARC[head], int32_peak,
-                            "32-bit integer pipe")
+    issue_peak = ISSUE_SLOTS_PER_SM_CLK * sm_count * SM_MAX_MHZ * 1e6
+    if head in INST_PER_ARC:
+        roofline = alu_roof(head_kernel_ms, INST_PER_ARC[head], issue_peak,
+                            "instruction issue (4 warp instructions per SM per clock)")
     elif head in FP64_OPS_PER_ARC:
         roofline = alu_roof(head_kernel_ms, FP64_OPS_PER_ARC[head], fp64_peak, "FP64 pipe")
     else:
@@ -335,9 +348,60 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if ragged is not None:
+        line["ragged_regridding"] = ragged
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def ragged_leg(sphx, torch, dev, args, head) -> dict:
+    """The regridding workload through the ragged call (not the headline): a
+    cubed sphere with 1024 x 1024 cells per face (12 595 200 edges) against
+    the 721 latitudes of a 0.25-degree grid. One step is the whole ragged
+    sequence (candidate ranges, prefix sum, persistent intersection with
+    compaction), replayed from the context's CUDA graph; the 605 MB of edges
+    exceed L2, so no flush is needed."""
+    A, B = W.cubed_sphere_edges(1024)
+    lat = W.latlon_latitudes(721)
+    E = len(A)
+    d = {"A": torch.from_numpy(A).to(dev), "B": torch.from_numpy(B).to(dev),
+         "eo": torch.tensor([0, E], dtype=torch.int64, device=dev),
+         "lat": torch.from_numpy(lat).to(dev),
+         "lo": torch.tensor([0, 721], dtype=torch.int64, device=dev)}
+    lo = torch.empty(E, dtype=torch.int32, device=dev)
+    hi = torch.empty(E, dtype=torch.int32, device=dev)
+    sphx.sphx_candidate_ranges(d["A"], d["B"], d["eo"], d["lat"], d["lo"], lo, hi)
+    pairs = int((hi - lo).sum().item())
+    cap = 2 * pairs + 1024
+    out = torch.empty(cap * 4, dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    res = {"workload": "cubed sphere N=1024 (12,595,200 edges) x 721 latitudes (0.25 deg)",
+           "edges": E, "candidate_pairs": pairs, "modes": {}}
+    cur = torch.cuda.current_stream(dev)
+    with sphx.Context(dev.index or 0) as ctx:
+        for mode in (head, "eft"):
+            for _ in range(args.warmup):
+                sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
+                                           total, mode, stream=cur)
+            if ctx.sync_status(cur) != sphx.OK:
+                raise RuntimeError("ragged call reported an error")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            for _ in range(args.steps):
+                sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
+                                           total, mode, stream=cur)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            hits = int(total.item())
+            res["hits"] = hits
+            res["modes"][mode] = {
+                "ms_per_step": ms, "edges_per_s": E / (ms * 1e-3),
+                "pairs_per_s": pairs / (ms * 1e-3), "hits_per_s": hits / (ms * 1e-3),
+                "hbm_frac": (48 * E + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak()}
+    return res
 
 
 def measured_hbm_peak() -> float:

@@ -148,9 +148,12 @@ sphx_status sphx_host_join(sphx_context *ctx, sphx_stream stream);
 /* Candidate latitude ranges of a ragged batch (step a11 of the hot path):
    for each edge e of mesh m, [lo[e], hi[e]) indexes lat_z (global indices)
    and covers every latitude of mesh m inside the edge's z-range (the endpoint
-   z's and, when the arc passes it, the arc's apex |n_xy| / |n|), widened by
-   1e-13 so that no hit is lost to rounding. lat_z must be sorted ascending
-   within each mesh. Sizes as in sphx_intersect_ragged. lo, hi: device int32[E]. */
+   z's and, when the arc passes it, the arc's apex |n_xy| / |n|, Sec. 2),
+   widened so that no hit is lost to rounding: by 2^-19 when both endpoints
+   have unit norm (the range is then computed in FP32, whose error stays three
+   times below the widening), by 1e-13 otherwise (FP64). lat_z must be sorted
+   ascending within each mesh. Sizes as in sphx_intersect_ragged.
+   lo, hi: device int32[E]. */
 sphx_status sphx_candidate_ranges(const double *A, const double *B, const int64_t *edge_offsets,
                                   int32_t M, int64_t E, const double *lat_z,
                                   const int64_t *lat_offsets, int64_t L, int32_t *lo,

@@ -3,9 +3,10 @@
 // per-pair evaluation of intersect.cuh).
 //
 //  1. candidate_kernel  per edge: z-range of the arc (endpoint z's, and the
-//                       apex +-|n_xy|/|n| when the arc passes it), widened,
-//                       then two binary searches into the mesh's sorted
-//                       latitudes give [lo, hi).
+//                       apex +-|n_xy|/|n| when the arc passes it), widened
+//                       (FP32 for unit endpoints, FP64 otherwise), then two
+//                       binary searches into the mesh's sorted latitudes
+//                       give [lo, hi).
 //  2. scan_*            exclusive prefix sum of hi - lo over all edges
 //                       (int64): pair p belongs to the edge e with
 //                       offsets[e] <= p < offsets[e + 1].
@@ -52,6 +53,92 @@ __device__ __forceinline__ int64_t lower_bound_dev(const double *a, int64_t n, d
 
 constexpr double kZWiden = 1e-13;
 
+// z-range of the minor arc x1 -> x2 in FP64: the endpoints' z and, when the
+// arc passes it, the great circle's highest (or lowest) point +-|n_xy| / |n|,
+// widened by 1e-13; false for a degenerate or non-finite arc
+__device__ __forceinline__ bool z_range_fp64(const double (&x1)[3], const double (&x2)[3],
+                                             double &zmin, double &zmax) {
+    double n[3], en[3];
+    accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
+    accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
+    accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
+    if (!finite7(x1, x2, 0.0) || (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0)) return false;
+    const double z1 = x1[2] * rsqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
+    const double z2 = x2[2] * rsqrt(x2[0] * x2[0] + x2[1] * x2[1] + x2[2] * x2[2]);
+    zmin = fmin(z1, z2);
+    zmax = fmax(z1, z2);
+    // scale n to avoid underflow in the squares of very short arcs
+    const double amax = fmax(fabs(n[0]), fmax(fabs(n[1]), fabs(n[2])));
+    const double sc = ldexp(1.0, -exponent_of(amax));
+    const double nx = n[0] * sc, ny = n[1] * sc, nz = n[2] * sc;
+    const double S2 = nx * nx + ny * ny, S3 = S2 + nz * nz;
+    // highest point of the great circle: a = (-nx nz, -ny nz, S2); it is on
+    // the arc iff a . (n x x1) >= 0 and a . (x2 x n) >= 0 (the lowest is -a)
+    const double ax = -nx * nz, ay = -ny * nz, az = S2;
+    const double m1x = ny * x1[2] - nz * x1[1], m1y = nz * x1[0] - nx * x1[2],
+                 m1z = nx * x1[1] - ny * x1[0];
+    const double m2x = x2[1] * nz - x2[2] * ny, m2y = x2[2] * nx - x2[0] * nz,
+                 m2z = x2[0] * ny - x2[1] * nx;
+    const double t1 = ax * m1x + ay * m1y + az * m1z;
+    const double t2 = ax * m2x + ay * m2y + az * m2z;
+    const double zap = sqrt(S2 / S3);
+    if (t1 >= 0.0 && t2 >= 0.0) zmax = zap;
+    if (t1 <= 0.0 && t2 <= 0.0) zmin = -zap;
+    zmin -= kZWiden;
+    zmax += kZWiden;
+    return true;
+}
+
+// The same z-range in FP32 for endpoints of unit norm (to 2^-20), widened by
+// kZWiden32. With d = x2 - x1 (or x2 + x1 when x1 . x2 < 0) from one FP64
+// subtraction per component, n = x1 x d equals x1 x x2 and stays
+// well-conditioned for short and for nearly antipodal arcs (d makes an angle
+// of at least 45 degrees with x1), so every FP32 quantity below -- the
+// endpoints' z, n, |n_xy|^2, |n|^2 and the apex height |n_xy| / |n| -- is
+// within a few units of 2^-24 of its exact value: at most about 6e-7 in z,
+// three times below the widening. A wrong apex decision needs the apex within
+// about 1e-6 rad of an endpoint, where the two heights differ by ~1e-12.
+// Returns false when the fast path does not apply (non-unit or non-finite
+// endpoints, or |n| below the FP32 range).
+constexpr float kZWiden32 = 1.0f / (1 << 19);
+
+__device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
+                                             double &zmin, double &zmax) {
+    float p1[3], p2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p1[i] = f32_scaled(x1[i], 0);
+        p2[i] = f32_scaled(x2[i], 0);
+    }
+    const float q1 = p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2];
+    const float q2 = p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2];
+    if (!(fabsf(q1 - 1.0f) < 1e-6f && fabsf(q2 - 1.0f) < 1e-6f)) return false;
+    const double sg = (p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f) ? 1.0 : -1.0;
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = f32_scaled(x2[i] - sg * x1[i], 0);
+    const float nx = fmaf(p1[1], d[2], -p1[2] * d[1]);
+    const float ny = fmaf(p1[2], d[0], -p1[0] * d[2]);
+    const float nz = fmaf(p1[0], d[1], -p1[1] * d[0]);
+    const float S2 = fmaf(nx, nx, ny * ny), S3 = fmaf(nz, nz, S2);
+    if (!(S3 > 1e-30f)) return false;
+    const float z1 = p1[2] * rsqrtf(q1), z2 = p2[2] * rsqrtf(q2);
+    float lo = fminf(z1, z2), hi = fmaxf(z1, z2);
+    const float ax = -nx * nz, ay = -ny * nz, az = S2;
+    const float m1x = fmaf(ny, p1[2], -nz * p1[1]), m1y = fmaf(nz, p1[0], -nx * p1[2]),
+                m1z = fmaf(nx, p1[1], -ny * p1[0]);
+    const float m2x = fmaf(p2[1], nz, -p2[2] * ny), m2y = fmaf(p2[2], nx, -p2[0] * nz),
+                m2z = fmaf(p2[0], ny, -p2[1] * nx);
+    const float t1 = fmaf(ax, m1x, fmaf(ay, m1y, az * m1z));
+    const float t2 = fmaf(ax, m2x, fmaf(ay, m2y, az * m2z));
+    const float zap = sqrtf(S2 / S3);
+    if (t1 >= 0.0f && t2 >= 0.0f) hi = zap;
+    if (t1 <= 0.0f && t2 <= 0.0f) lo = -zap;
+    zmin = (double)(lo - kZWiden32);
+    zmax = (double)(hi + kZWiden32);
+    return true;
+}
+
 __global__ void candidate_kernel(const double *__restrict__ A, const double *__restrict__ B,
                                  const int64_t *__restrict__ edge_offsets, int M, int64_t E,
                                  const double *__restrict__ lat_z, int64_t L,
@@ -69,34 +156,10 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
         const double x1[3] = {A[3 * e], A[3 * e + 1], A[3 * e + 2]};
         const double x2[3] = {B[3 * e], B[3 * e + 1], B[3 * e + 2]};
         int32_t lo = (int32_t)ls, hi = (int32_t)ls;
-        double n[3], en[3];
-        accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
-        accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
-        accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
-        const bool ok = finite7(x1, x2, 0.0) && (n[0] != 0.0 || n[1] != 0.0 || n[2] != 0.0);
-        if (ok) {
-            const double z1 = x1[2] * rsqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
-            const double z2 = x2[2] * rsqrt(x2[0] * x2[0] + x2[1] * x2[1] + x2[2] * x2[2]);
-            double zmin = fmin(z1, z2), zmax = fmax(z1, z2);
-            // scale n to avoid underflow in the squares of very short arcs
-            const double amax = fmax(fabs(n[0]), fmax(fabs(n[1]), fabs(n[2])));
-            const double sc = ldexp(1.0, -exponent_of(amax));
-            const double nx = n[0] * sc, ny = n[1] * sc, nz = n[2] * sc;
-            const double S2 = nx * nx + ny * ny, S3 = S2 + nz * nz;
-            // highest point of the great circle: a = (-nx nz, -ny nz, S2); it is on
-            // the arc iff a . (n x x1) >= 0 and a . (x2 x n) >= 0 (the lowest is -a)
-            const double ax = -nx * nz, ay = -ny * nz, az = S2;
-            const double m1x = ny * x1[2] - nz * x1[1], m1y = nz * x1[0] - nx * x1[2],
-                         m1z = nx * x1[1] - ny * x1[0];
-            const double m2x = x2[1] * nz - x2[2] * ny, m2y = x2[2] * nx - x2[0] * nz,
-                         m2z = x2[0] * ny - x2[1] * nx;
-            const double t1 = ax * m1x + ay * m1y + az * m1z;
-            const double t2 = ax * m2x + ay * m2y + az * m2z;
-            const double zap = sqrt(S2 / S3);
-            if (t1 >= 0.0 && t2 >= 0.0) zmax = zap;
-            if (t1 <= 0.0 && t2 <= 0.0) zmin = -zap;
-            zmin -= kZWiden;
-            zmax += kZWiden;
+        double zmin, zmax;
+        const bool finite = finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) &&
+                            finite_bits(x2[0]) && finite_bits(x2[1]) && finite_bits(x2[2]);
+        if (finite && (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
             const double *lz = lat_z + ls;
             lo = (int32_t)(ls + lower_bound_dev(lz, le - ls, zmin));
             hi = (int32_t)(ls + upper_bound_dev<double>(lz, le - ls, zmax));
@@ -210,6 +273,30 @@ __device__ __forceinline__ unsigned long long lb_pack(unsigned long long flag,
 
 
 
+// first index i in [0, n) with a[i] > key (n if none), found by the whole
+// warp: each round probes 32 evenly spaced positions at once and narrows the
+// interval to one of the 32 gaps (a monotone array makes the probes <= key a
+// prefix of the lanes), so a search over n entries takes log32(n) rounds of
+// parallel loads instead of log2(n) dependent ones
+__device__ __forceinline__ int64_t warp_upper_bound(const long long *a, int64_t n, long long key,
+                                                    int lane) {
+    int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t pos = lo + (int64_t)lane * step;
+        const bool le = pos < hi && a[pos] <= key;
+        const int c = __popc(__ballot_sync(0xffffffffu, le));
+        if (c == 0) return lo;
+        const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+        const int64_t nhi = lo + (int64_t)c * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    const int64_t pos = lo + lane;
+    const bool le = pos < hi && a[pos] <= key;
+    return lo + __popc(__ballot_sync(0xffffffffu, le));
+}
+
 template <int Mode, int K, bool Ordered>
 __global__ void ragged_kernel(RaggedArgs a) {
     const int lane = threadIdx.x & 31;
@@ -224,14 +311,10 @@ __global__ void ragged_kernel(RaggedArgs a) {
         if ((long long)c >= nchunks) break;
         const long long p0 = (long long)c * CH;
         const long long p1 = min(p0 + CH, T);
-        // edges of the first and last pair of the chunk
-        long long ef = 0;
-        if (lane < 2) {
-            const long long key = lane == 0 ? p0 : p1 - 1;
-            ef = upper_bound_dev<long long>(a.offsets, a.E + 1, key) - 1;
-        }
-        const long long e_first = __shfl_sync(0xffffffffu, ef, 0);
-        const long long e_last = __shfl_sync(0xffffffffu, ef, 1);
+        // edges of the first and last pair of the chunk (warp-cooperative searches)
+        const long long e_first = warp_upper_bound(a.offsets, a.E + 1, p0, lane) - 1;
+        const long long e_last =
+            e_first + warp_upper_bound(a.offsets + e_first, a.E + 1 - e_first, p1 - 1, lane) - 1;
         PairOut res[K];
         long long edge[K];
         int32_t lat[K];
