@@ -47,7 +47,11 @@ BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
 # thread instructions per arc of dense_kernel<WIDE> (ncu smsp__inst_executed.sum x 32
 # / arcs on the 10^6-arc stress workload): the integer-limb method's work per arc
-INST_PER_ARC = {"wide": 2560}
+INST_PER_ARC = {"wide": 2492}
+# DRAM bytes (read + write) of one launch of the headline kernel over the 10^6
+# stress arcs, from the same ncu capture (writes still in L2 at kernel end are
+# not counted)
+TRAFFIC_PER_LAUNCH = {"wide": 56.064e6 + 9.124e6}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
@@ -327,6 +331,7 @@ def main():
     else:
         roofline = hbm_roof(head_kernel_ms)
     roofline["kernel"] = f"dense_kernel<{head}>"
+    roofline["traffic"] = TRAFFIC_PER_LAUNCH.get(head)
     per_mode_roofs = {"hbm": {m: hbm_roof(modes[m]["ms_per_step"])["frac"] for m in modes}}
     per_mode_roofs["fp64_pipe"] = {m: alu_roof(modes[m]["ms_per_step"], FP64_OPS_PER_ARC[m],
                                                fp64_peak, "FP64")["frac"]

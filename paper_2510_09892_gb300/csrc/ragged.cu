@@ -38,17 +38,49 @@ __device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t n, T key)
     }
     return lo;
 }
-// first index i in [0, n) with a[i] >= key
-__device__ __forceinline__ int64_t lower_bound_dev(const double *a, int64_t n, double key) {
+// An order-preserving integer image of a double (not NaN): comparing the
+// images compares the values, with no FP64 instruction (GB300 issues FP64
+// comparisons at 2 per SM per clock, 64-bit integer ones far faster).
+// -0.0 maps just below +0.0, which only matters for keys that widen a range.
+__device__ __forceinline__ long long ord64(double x) {
+    const long long b = (long long)wide::bits_of(x);
+    return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+
+// first index i in [0, n) with a[i] >= key (by ord64)
+__device__ __forceinline__ int64_t lower_bound_ord(const double *a, int64_t n, long long key) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
-        if (a[mid] >= key)
+        if (ord64(a[mid]) >= key)
             hi = mid;
         else
             lo = mid + 1;
     }
     return lo;
+}
+
+// first index i in [0, n) with a[i] > key (by ord64)
+__device__ __forceinline__ int64_t upper_bound_ord(const double *a, int64_t n, long long key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (ord64(a[mid]) > key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// a float in [-2, 2] as a double, by its bits (values below 2^-126 become +-0)
+__device__ __forceinline__ double f64_of_f32_small(float f) {
+    const uint32_t b = wide::fbits_of(f);
+    const uint32_t fe = (b >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+    if (fe == 0) return wide::double_of(sign);
+    return wide::double_of(sign | ((uint64_t)(fe - 127u + 1023u) << 52) |
+                           ((uint64_t)(b & 0x7fffffu) << 29));
 }
 
 constexpr double kZWiden = 1e-13;
@@ -134,8 +166,8 @@ __device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double
     const float zap = sqrtf(S2 / S3);
     if (t1 >= 0.0f && t2 >= 0.0f) hi = zap;
     if (t1 <= 0.0f && t2 <= 0.0f) lo = -zap;
-    zmin = (double)(lo - kZWiden32);
-    zmax = (double)(hi + kZWiden32);
+    zmin = f64_of_f32_small(lo - kZWiden32);
+    zmax = f64_of_f32_small(hi + kZWiden32);
     return true;
 }
 
@@ -161,8 +193,8 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
                             finite_bits(x2[0]) && finite_bits(x2[1]) && finite_bits(x2[2]);
         if (finite && (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
             const double *lz = lat_z + ls;
-            lo = (int32_t)(ls + lower_bound_dev(lz, le - ls, zmin));
-            hi = (int32_t)(ls + upper_bound_dev<double>(lz, le - ls, zmax));
+            lo = (int32_t)(ls + lower_bound_ord(lz, le - ls, ord64(zmin)));
+            hi = (int32_t)(ls + upper_bound_ord(lz, le - ls, ord64(zmax)));
             if (hi < lo) hi = lo;
         }
         lo_out[e] = lo;
@@ -243,22 +275,40 @@ __global__ void __launch_bounds__(kScanThreads)
     scan_apply(const int32_t *__restrict__ lo, const int32_t *__restrict__ hi, int64_t E,
                const long long *__restrict__ block_sums, long long *__restrict__ offsets) {
     __shared__ long long ws[32];
-    const int64_t base = blockIdx.x * (int64_t)kScanTile + (int64_t)threadIdx.x * kScanItems;
+    // the block's counts, then their exclusive scan; one pad slot per 16 so
+    // that the per-thread runs of 16 fall in different banks
+    __shared__ long long tile[kScanTile + kScanTile / 16];
+    const int64_t base = blockIdx.x * (int64_t)kScanTile;
+    // coalesced loads into shared memory ...
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int idx = i * kScanThreads + threadIdx.x;
+        const int64_t e = base + idx;
+        tile[idx + (idx >> 4)] = e < E ? count_of(lo, hi, e) : 0;
+    }
+    __syncthreads();
+    // ... each thread scans its kScanItems consecutive counts ...
     long long c[kScanItems];
     long long s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
-        c[i] = e < E ? count_of(lo, hi, e) : 0;
+        c[i] = tile[threadIdx.x * (kScanItems + 1) + i];
         s += c[i];
     }
     long long total;
     long long ex = block_exclusive_scan<long long>(s, ws, total) + block_sums[blockIdx.x];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
-        if (e < E) offsets[e] = ex;
+        tile[threadIdx.x * (kScanItems + 1) + i] = ex;
         ex += c[i];
+    }
+    __syncthreads();
+    // ... and coalesced stores
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int idx = i * kScanThreads + threadIdx.x;
+        const int64_t e = base + idx;
+        if (e < E) offsets[e] = tile[idx + (idx >> 4)];
     }
 }
 
