@@ -55,13 +55,16 @@ typedef enum {
        SumOfSquaresC for arcs much shorter than 1e-8 rad or nearly antipodal).
        Error <= 4 ulp per component of the correctly rounded exact point. */
     SPHX_MODE_EFT_FP64 = 1,
-    /* float-float: the normal by FP64 AccuDOP, rescaled by an exact power of
-       two; squared norms, s^2, s and the numerators in pairs of FP32 with
-       TwoSum / FMA TwoProd; the final divisions and the containment test in
-       FP64. s^2 carries about 48 bits, so the error grows near tangency and
-       near the poles: |P~ - P| <= 2 (2^-44 sqrt(1 - z0^2)
-       + 2^-48 |n|^2 / (|n_xy| s)); hit counts can differ from the exact ones
-       where s^2 is below that resolution. */
+    /* float-float (pairs of FP32 with TwoSum / FMA TwoProd) for endpoints of
+       unit norm: d = x2 -+ x1 in FP64 (the cancelling part of the cross
+       product of nearly coincident or antipodal endpoints), n = x1 x d,
+       |n_xy|^2, |n|^2, s^2, the square root, 1 / |n_xy|^2 and the point in
+       float-float on the FP32 pipe; the on-arc test on FP64 offsets from the
+       endpoints. s^2 carries about 46 bits, so the error grows near tangency
+       and near the poles: |P~ - P| <= 2^-44 sqrt(1 - z0^2)
+       + 2^-45 |n|^2 / (|n_xy| s); hit counts can differ from the exact ones
+       where s^2 is below that resolution. Other endpoints are evaluated as in
+       SPHX_MODE_WIDE_INT. */
     SPHX_MODE_EFT_FF32 = 2,
     /* Algorithm 8 exactly as printed (no renormalisation after AccuDOP), for
        comparison; loses accuracy on very short and near-antipodal arcs. */

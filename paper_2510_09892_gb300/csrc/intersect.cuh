@@ -15,6 +15,7 @@
 //               (P x x2).n >= 0: P between x1 and x2 on the minor arc).
 #pragma once
 #include "eft.cuh"
+#include "ff.cuh"
 #include "wide.cuh"
 
 namespace sphx {
@@ -425,6 +426,109 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
     }
 }
 
+// ---- float-float, FP64 only where stability needs it ---------------------------
+// For endpoints of unit norm. The cross product of nearly coincident or nearly
+// antipodal endpoints cancels: d = x2 - x1 (or x2 + x1 when x1 . x2 < 0) is
+// formed in FP64 (one subtraction per component, exact or one rounding) and
+// n = x1 x d = x1 x x2 in float-float, where it is well-conditioned (d makes
+// an angle of at least 45 degrees with x1). |n_xy|^2, |n|^2, s^2, the square
+// root, 1 / |n_xy|^2 and P = g n_xy +- h (n_y, -n_x) (g = -z0 n_z / |n_xy|^2,
+// h = -s / |n_xy|^2, Eq. 2.2) follow in float-float on the FP32 pipe; the
+// on-arc test is that of pair_wide with l = +-1. s^2 carries about 46 bits,
+// so accuracy degrades near tangency and near the poles like that of any
+// fixed-precision evaluation of Eq. 2.2 (stated bound in the header). Other
+// endpoints go to pair_wide.
+
+// x 2^k for a finite double, by its bits (0 when the result leaves the normal range)
+SPHX_HD double scale_pow2(double x, int k) {
+    const uint64_t b = wide::bits_of(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0 || ex + k <= 0) return 0.0;
+    return wide::double_of(b + ((uint64_t)(int64_t)k << 52));
+}
+
+SPHX_HD void pair_ff2(const double (&x1)[3], const double (&x2)[3], double z0, PairOut &o) {
+    using namespace ffa;
+    if (!(finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) && finite_bits(x2[0]) &&
+          finite_bits(x2[1]) && finite_bits(x2[2]) && finite_bits(z0)))
+        return clear(o, 0);
+    float p1[3], p2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        p1[i] = f32_scaled(x1[i], 0);
+        p2[i] = f32_scaled(x2[i], 0);
+    }
+    const float q1 = wide::fma32(p1[0], p1[0], wide::fma32(p1[1], p1[1], p1[2] * p1[2]));
+    const float q2 = wide::fma32(p2[0], p2[0], wide::fma32(p2[1], p2[1], p2[2] * p2[2]));
+    if (!(fabsf(q1 - 1.0f) < 1e-6f && fabsf(q2 - 1.0f) < 1e-6f)) return pair_wide(x1, x2, z0, o);
+    const bool same = p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f;
+    double d[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = same ? x2[i] - x1[i] : x2[i] + x1[i];
+    int E = exponent_bits(d[0]);
+    E = exponent_bits(d[1]) > E ? exponent_bits(d[1]) : E;
+    E = exponent_bits(d[2]) > E ? exponent_bits(d[2]) : E;
+    if (E < -1022) return clear(o, -1);  // d = 0: x2 = +-x1, n = 0
+    F2 X[3], D[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        X[i] = split(x1[i]);
+        D[i] = split(scale_pow2(d[i], -E));  // max |d_i| in [1, 2)
+    }
+    const F2 nx = add2(mul2(X[1], D[2]), neg(mul2(X[2], D[1])));
+    const F2 ny = add2(mul2(X[2], D[0]), neg(mul2(X[0], D[2])));
+    const F2 nz = add2(mul2(X[0], D[1]), neg(mul2(X[1], D[0])));
+    if (nx.hi == 0.0f && ny.hi == 0.0f && nz.hi == 0.0f) return clear(o, -1);
+    const bool z0_zero = (wide::bits_of(z0) << 1) == 0;
+    if (nx.hi == 0.0f && ny.hi == 0.0f) return clear(o, z0_zero ? -1 : 0);
+    const F2 S2 = add2(sqr2(nx), sqr2(ny));
+    const F2 S3 = add2(S2, sqr2(nz));
+    const F2 Z = split(z0);
+    const F2 s2 = add2(S2, neg(mul2(S3, sqr2(Z))));
+    if (s2.hi < 0.0f) return clear(o, 0);
+    const bool tangent = s2.hi == 0.0f;
+    const F2 r = neg(rcp2(S2));  // -1 / |n_xy|^2
+    const F2 g = mul2(mul2(Z, nz), r);
+    const F2 h = tangent ? F2{0.0f, 0.0f} : mul2(sqrt2(s2), r);
+    const F2 gx = mul2(g, nx), gy = mul2(g, ny), hx = mul2(h, nx), hy = mul2(h, ny);
+
+    // on-arc test (as in pair_wide, endpoints of unit norm: l = +-1)
+    const float nf[3] = {nx.hi, ny.hi, nz.hi};
+    const float m1[3] = {wide::fma32(nf[1], p1[2], -nf[2] * p1[1]), wide::fma32(nf[2], p1[0], -nf[0] * p1[2]),
+                         wide::fma32(nf[0], p1[1], -nf[1] * p1[0])};
+    const float m2[3] = {wide::fma32(p2[1], nf[2], -p2[2] * nf[1]), wide::fma32(p2[2], nf[0], -p2[0] * nf[2]),
+                         wide::fma32(p2[0], nf[1], -p2[1] * nf[0])};
+    const float zf = f32_scaled(z0, 0);
+    const int nroots = tangent ? 1 : 2;
+    o.count = 0;
+#pragma unroll
+    for (int rt = 0; rt < 2; ++rt) {
+        o.hit[rt] = false;
+        if (rt >= nroots) continue;
+        const F2 X_ = add2(gx, rt == 0 ? hy : neg(hy));
+        const F2 Y_ = add2(gy, rt == 0 ? neg(hx) : hx);
+        const double Px = to_f64(X_.hi) + to_f64(X_.lo);
+        const double Py = to_f64(Y_.hi) + to_f64(Y_.lo);
+        o.px[rt] = Px;
+        o.py[rt] = Py;
+        const float pf[3] = {X_.hi, Y_.hi, zf};
+        const bool n1 = pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f;
+        const bool n2 = pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f;
+        const float d1[3] = {f32_scaled(n1 ? Px - x1[0] : Px + x1[0], 0),
+                             f32_scaled(n1 ? Py - x1[1] : Py + x1[1], 0),
+                             f32_scaled(n1 ? z0 - x1[2] : z0 + x1[2], 0)};
+        const float d2[3] = {f32_scaled(n2 ? Px - x2[0] : Px + x2[0], 0),
+                             f32_scaled(n2 ? Py - x2[1] : Py + x2[1], 0),
+                             f32_scaled(n2 ? z0 - x2[2] : z0 + x2[2], 0)};
+        const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
+        const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));
+        if (t1 >= 0.0f && t2 >= 0.0f) {
+            o.hit[rt] = true;
+            ++o.count;
+        }
+    }
+}
+
 template <int Mode>
 __device__ __forceinline__ void intersect_pair(const double (&x1)[3], const double (&x2)[3],
                                                double z0, PairOut &o) {
@@ -437,7 +541,7 @@ __device__ __forceinline__ void intersect_pair(const double (&x1)[3], const doub
     else if (Mode == kWideInt)
         pair_wide(x1, x2, z0, o);
     else
-        pair_ff32(x1, x2, z0, o);
+        pair_ff2(x1, x2, z0, o);
 }
 
 }  // namespace sphx

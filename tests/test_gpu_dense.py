@@ -22,10 +22,10 @@ from tests import parity as P
 
 pytestmark = pytest.mark.gpu
 
-# float-float's stated bound (s^2 carries about 48 bits, so its absolute error
-# near 2^-48 |n|^2 is amplified by 1 / (2 s) near tangency and near the poles):
-#   |P~ - P| <= FF_C * (2^-44 sqrt(1 - z0^2) + 2^-48 |n|^2 / (|n_xy| s))
-FF_C = 2.0
+# float-float's stated bound (s^2 carries about 46 bits, so its absolute error
+# near 2^-46 |n|^2 is amplified by 1 / (2 s) near tangency and near the poles):
+#   |P~ - P| <= 2^-44 sqrt(1 - z0^2) + 2^-45 |n|^2 / (|n_xy| s)
+FF_RHO, FF_COND = 2.0 ** -44, 2.0 ** -45
 
 
 def run(A, B, z, mode):
@@ -141,7 +141,7 @@ def _ff_bound(A, B, z):
     s = np.sqrt(np.maximum(nxy ** 2 - S3 * z * z, 0))
     rho = np.sqrt(np.maximum(0.0, (1 - z) * (1 + z)))
     with np.errstate(divide="ignore"):
-        b = FF_C * (2.0 ** -44 * rho + 2.0 ** -48 * S3 / (nxy * s))
+        b = FF_RHO * rho + FF_COND * S3 / (nxy * s)
     return b / (P.U * np.maximum(rho, 1e-300))
 
 
