@@ -462,9 +462,12 @@ SPHX_HD void pair_ff2(const double (&x1)[3], const double (&x2)[3], double z0, P
     const float q2 = wide::fma32(p2[0], p2[0], wide::fma32(p2[1], p2[1], p2[2] * p2[2]));
     if (!(fabsf(q1 - 1.0f) < 1e-6f && fabsf(q2 - 1.0f) < 1e-6f)) return pair_wide(x1, x2, z0, o);
     const bool same = p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f;
+    // one FMA per component with a +-1 factor (a select between x2 - x1 and
+    // x2 + x1 would evaluate both on the FP64 pipe)
+    const double sg = same ? 1.0 : -1.0;
     double d[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = same ? x2[i] - x1[i] : x2[i] + x1[i];
+    for (int i = 0; i < 3; ++i) d[i] = wide::fma64(-sg, x1[i], x2[i]);
     int E = exponent_bits(d[0]);
     E = exponent_bits(d[1]) > E ? exponent_bits(d[1]) : E;
     E = exponent_bits(d[2]) > E ? exponent_bits(d[2]) : E;
@@ -514,12 +517,13 @@ SPHX_HD void pair_ff2(const double (&x1)[3], const double (&x2)[3], double z0, P
         const float pf[3] = {X_.hi, Y_.hi, zf};
         const bool n1 = pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f;
         const bool n2 = pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f;
-        const float d1[3] = {f32_scaled(n1 ? Px - x1[0] : Px + x1[0], 0),
-                             f32_scaled(n1 ? Py - x1[1] : Py + x1[1], 0),
-                             f32_scaled(n1 ? z0 - x1[2] : z0 + x1[2], 0)};
-        const float d2[3] = {f32_scaled(n2 ? Px - x2[0] : Px + x2[0], 0),
-                             f32_scaled(n2 ? Py - x2[1] : Py + x2[1], 0),
-                             f32_scaled(n2 ? z0 - x2[2] : z0 + x2[2], 0)};
+        const double l1 = n1 ? 1.0 : -1.0, l2 = n2 ? 1.0 : -1.0;
+        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0),
+                             f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
+                             f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
+        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0),
+                             f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
+                             f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
         const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
         const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));
         if (t1 >= 0.0f && t2 >= 0.0f) {
