@@ -273,6 +273,25 @@ def polygon_mesh(rng, n_edges: int):
     return np.ascontiguousarray(A), np.ascontiguousarray(B)
 
 
+def ragged_sizes(n_mesh: int, e_min: float, e_max: float, seed: int = DEFAULT_SEED + 3,
+                 lat_min: int = 180, lat_max: int = 2881):
+    """Edge counts (log-uniform in [e_min, e_max]) and latitude counts (uniform
+    in [lat_min, lat_max]) of a mesh batch."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0]))
+    E = np.exp(rng.uniform(math.log(e_min), math.log(e_max), n_mesh)).astype(np.int64)
+    E = np.maximum(E, 1)
+    L = rng.integers(lat_min, lat_max + 1, n_mesh)
+    return E, L
+
+
+def ragged_mesh(args):
+    """Mesh m of a batch, (m, n_edges, seed) -> (A, B): seeded on its own, so
+    the meshes of a batch can be generated independently (in parallel)."""
+    m, n_edges, seed = args
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 1, int(m)]))
+    return polygon_mesh(rng, int(n_edges))
+
+
 def ragged_meshes(n_mesh: int, e_min: float, e_max: float, seed: int = DEFAULT_SEED + 3,
                   lat_min: int = 180, lat_max: int = 2881):
     """A batch of independent polygon meshes with per-mesh latitude grids.
@@ -281,13 +300,10 @@ def ragged_meshes(n_mesh: int, e_min: float, e_max: float, seed: int = DEFAULT_S
     [lat_min, lat_max]. Returns dict with A, B (E,3), edge_offsets (M+1,),
     lat_z (sum L,), lat_offsets (M+1,).
     """
-    rng = np.random.default_rng(seed)
-    E = np.exp(rng.uniform(math.log(e_min), math.log(e_max), n_mesh)).astype(np.int64)
-    E = np.maximum(E, 1)
-    L = rng.integers(lat_min, lat_max + 1, n_mesh)
+    E, L = ragged_sizes(n_mesh, e_min, e_max, seed, lat_min, lat_max)
     A_parts, B_parts, Z_parts = [], [], []
     for m in range(n_mesh):
-        a, b = polygon_mesh(rng, int(E[m]))
+        a, b = ragged_mesh((m, E[m], seed))
         A_parts.append(a)
         B_parts.append(b)
         Z_parts.append(latlon_latitudes(int(L[m])))
