@@ -222,10 +222,14 @@ def main():
         return run_reference(args)
 
     rank, world, local = dist_env()
-    # the oracle's process pool starts before CUDA does ('spawn' regardless)
+    # the process pools start before CUDA does ('spawn' regardless)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
+    mesh_pool = None
+    if rank == 0 and not args.no_ragged:
+        import multiprocessing as mp
+        mesh_pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
 
     import torch
     import torch.distributed as dist
@@ -297,6 +301,8 @@ def main():
     clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
 
     ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
+    meshes = (meshes_leg(sphx, torch, dev, args, head, mesh_pool)
+              if rank == 0 and not args.no_ragged else None)
 
     # hits per step, from one more headline call's outputs
     sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, head)
@@ -355,6 +361,8 @@ def main():
         line["cpu_baseline"] = cpu
     if ragged is not None:
         line["ragged_regridding"] = ragged
+    if meshes is not None:
+        line["ragged_meshes"] = meshes
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -406,6 +414,70 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
                 "ms_per_step": ms, "edges_per_s": E / (ms * 1e-3),
                 "pairs_per_s": pairs / (ms * 1e-3), "hits_per_s": hits / (ms * 1e-3),
                 "hbm_frac": (48 * E + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak()}
+    return res
+
+
+def meshes_leg(sphx, torch, dev, args, head, pool) -> dict:
+    """Ragged batching (not the headline): 512 independent polygon meshes of
+    10^3 - 5x10^6 edges (log-uniform, ~3x10^8 edges in all) against per-mesh
+    grids of 180 - 2881 latitudes, in one persistent launch replayed from a
+    CUDA graph, with the launch shape picked by sphx_autotune_ragged."""
+    E, L = W.ragged_sizes(512, 1e3, 5e6)
+    eo = np.concatenate([[0], np.cumsum(E)]).astype(np.int64)
+    lo_ = np.concatenate([[0], np.cumsum(L)]).astype(np.int64)
+    lat = np.concatenate([W.latlon_latitudes(int(x)) for x in L])
+    Et = int(eo[-1])
+    tA = torch.empty((Et, 3), dtype=torch.float64, device=dev)
+    tB = torch.empty((Et, 3), dtype=torch.float64, device=dev)
+    seed = W.DEFAULT_SEED + 3
+    with pool:
+        for m, (A, B) in enumerate(pool.imap(W.ragged_mesh, [(m, int(E[m]), seed)
+                                                            for m in range(len(E))])):
+            tA[int(eo[m]):int(eo[m + 1])].copy_(torch.from_numpy(A))
+            tB[int(eo[m]):int(eo[m + 1])].copy_(torch.from_numpy(B))
+    teo = torch.from_numpy(eo).to(dev)
+    tlo = torch.from_numpy(lo_).to(dev)
+    tlat = torch.from_numpy(lat).to(dev)
+    lo = torch.empty(Et, dtype=torch.int32, device=dev)
+    hi = torch.empty(Et, dtype=torch.int32, device=dev)
+    sphx.sphx_candidate_ranges(tA, tB, teo, tlat, tlo, lo, hi)
+    pairs = int((hi - lo).sum().item())
+    del lo, hi
+    cap = pairs + pairs // 8 + 4096
+    out = torch.empty(cap * 4, dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    res = {"workload": "512 polygon meshes, 1e3-5e6 edges each (log-uniform), 180-2881 "
+                       "latitudes per mesh", "edges": Et, "candidate_pairs": pairs, "modes": {}}
+    cur = torch.cuda.current_stream(dev)
+    with sphx.Context(dev.index or 0) as ctx:
+        for mode in (head, "eft"):
+            ctx.reset_tuning()
+            tune_ms = sphx.sphx_autotune_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
+                                                stream=cur)
+            for _ in range(3):
+                sphx.sphx_intersect_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
+                                           stream=cur)
+            if ctx.sync_status(cur) != sphx.OK:
+                raise RuntimeError("ragged call reported an error")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            steps = max(3, args.steps // 4)
+            e0.record(cur)
+            for _ in range(steps):
+                sphx.sphx_intersect_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
+                                           stream=cur)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            hits = int(total.item())
+            res["hits"] = hits
+            res["modes"][mode] = {
+                "ms_per_step": ms, "edges_per_s": Et / (ms * 1e-3),
+                "pairs_per_s": pairs / (ms * 1e-3), "hits_per_s": hits / (ms * 1e-3),
+                "hbm_frac": (48 * Et + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak(),
+                "tuning": ctx.get_tuning(), "autotune_best_ms": tune_ms}
+    del tA, tB, out
+    torch.cuda.empty_cache()
     return res
 
 
