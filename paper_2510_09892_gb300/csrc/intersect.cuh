@@ -154,127 +154,6 @@ __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (
     }
 }
 
-// ---- float-float -------------------------------------------------------------
-// Pairs of FP32 (hi + lo, |lo| <= 2^-24 |hi|) carry about 48 bits.
-struct ff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ ff ff_from(double v) {
-    float h = __double2float_rn(v);
-    float l = __double2float_rn(sub(v, (double)h));
-    return {h, l};
-}
-// v + e (both FP64, |e| << |v|) as float-float
-__device__ __forceinline__ ff ff_from2(double v, double e) {
-    float h = __double2float_rn(v);
-    float l = __double2float_rn(add(sub(v, (double)h), e));
-    return {h, l};
-}
-__device__ __forceinline__ ff ff_norm(float s, float e) {
-    ff r;
-    fast_two_sum(s, e, r.hi, r.lo);
-    return r;
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    float s, e;
-    two_sum(a.hi, b.hi, s, e);
-    e = add(e, add(a.lo, b.lo));
-    return ff_norm(s, e);
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    float p, e;
-    two_prod(a.hi, b.hi, p, e);
-    e = fma_(a.hi, b.lo, e);
-    e = fma_(a.lo, b.hi, e);
-    return ff_norm(p, e);
-}
-__device__ __forceinline__ ff ff_sqr(ff a) {
-    float p, e;
-    two_prod(a.hi, a.hi, p, e);
-    e = fma_(add(a.hi, a.hi), a.lo, e);
-    return ff_norm(p, e);
-}
-// sqrt of a non-negative float-float (double-word square root, as acc_sqrt)
-__device__ __forceinline__ ff ff_sqrt(ff a) {
-    if (a.hi <= 0.0f) return {0.0f, 0.0f};
-    float r = sqrt_(a.hi);
-    float rem = fma_(-r, r, a.hi);
-    float l = div_(add(rem, a.lo), add(r, r));
-    return ff_norm(r, l);
-}
-__device__ __forceinline__ double ff_to_double(ff a) { return add((double)a.hi, (double)a.lo); }
-
-// binary exponent of |v| for a finite nonzero double (floor(log2 |v|))
-__device__ __forceinline__ int exponent_of(double v) {
-    int hi = __double2hiint(v);
-    int ex = (hi >> 20) & 0x7ff;
-    if (ex == 0) return ilogb(v);  // subnormal
-    return ex - 1023;
-}
-
-__device__ __forceinline__ void pair_ff32(const double (&x1)[3], const double (&x2)[3], double z0,
-                                          PairOut &o) {
-    if (!finite7(x1, x2, z0)) return clear(o, 0);
-    // FP64: the compensated cross product (ill-conditioned for nearly parallel
-    // or antipodal endpoints), renormalised pairs
-    double n[3], en[3];
-    accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
-    accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
-    accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
-    if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return clear(o, -1);
-    if (n[0] == 0.0 && n[1] == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
-    // Eq. 2.2 is homogeneous of degree 0 in n: scale by an exact power of two
-    // so that max |n_i| lies in [1, 2) and FP32 neither underflows nor overflows
-    const double amax = fmax(fabs(n[0]), fmax(fabs(n[1]), fabs(n[2])));
-    const double sc = ldexp(1.0, -exponent_of(amax));
-    double ns[3];
-    ff nf[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        ns[i] = mul(n[i], sc);
-        nf[i] = ff_from2(ns[i], mul(en[i], sc));
-    }
-    const ff zf = ff_from(z0);
-    const ff S2 = ff_add(ff_sqr(nf[0]), ff_sqr(nf[1]));
-    const ff S3 = ff_add(S2, ff_sqr(nf[2]));
-    const ff s2 = ff_add(S2, ff_neg(ff_mul(S3, ff_sqr(zf))));
-    if (s2.hi < 0.0f) return clear(o, 0);
-    const ff s = ff_sqrt(s2);
-    const ff Ax = ff_mul(ff_mul(nf[0], nf[2]), zf);  // z0 n_x n_z
-    const ff Ay = ff_mul(ff_mul(nf[1], nf[2]), zf);  // z0 n_y n_z
-    const ff Bx = ff_mul(nf[1], s);                  // s n_y
-    const ff By = ff_mul(nf[0], s);                  // s n_x
-    const double S2d = ff_to_double(S2);
-    // containment in FP64 from the scaled leading parts
-    double m1x = fma_(ns[1], x1[2], -mul(ns[2], x1[1]));
-    double m1y = fma_(ns[2], x1[0], -mul(ns[0], x1[2]));
-    double m1z = fma_(ns[0], x1[1], -mul(ns[1], x1[0]));
-    double m2x = fma_(x2[1], ns[2], -mul(x2[2], ns[1]));
-    double m2y = fma_(x2[2], ns[0], -mul(x2[0], ns[2]));
-    double m2z = fma_(x2[0], ns[1], -mul(x2[1], ns[0]));
-    const int nroots = s2.hi > 0.0f ? 2 : 1;
-    o.count = 0;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        o.hit[r] = false;
-        if (r >= nroots) continue;
-        ff X = r == 0 ? ff_add(Ax, Bx) : ff_add(Ax, ff_neg(Bx));
-        ff Y = r == 0 ? ff_add(Ay, ff_neg(By)) : ff_add(Ay, By);
-        double Px = -div_(ff_to_double(X), S2d);
-        double Py = -div_(ff_to_double(Y), S2d);
-        double t1 = fma_(Px, m1x, fma_(Py, m1y, mul(z0, m1z)));
-        double t2 = fma_(Px, m2x, fma_(Py, m2y, mul(z0, m2z)));
-        o.px[r] = Px;
-        o.py[r] = Py;
-        if (t1 >= 0.0 && t2 >= 0.0) {
-            o.hit[r] = true;
-            ++o.count;
-        }
-    }
-}
-
 // ---- Eq. 2.2 in multi-limb integer arithmetic (wide.cuh) ----------------------
 // The normal n = x1 x x2 is formed from exact 106-bit products of the FP64
 // inputs and carried with 128-bit mantissas through |n_xy|^2, |n|^2 and

@@ -85,6 +85,14 @@ __device__ __forceinline__ double f64_of_f32_small(float f) {
 
 constexpr double kZWiden = 1e-13;
 
+// binary exponent of |v| for a finite nonzero double (floor(log2 |v|))
+__device__ __forceinline__ int exponent_of(double v) {
+    int hi = __double2hiint(v);
+    int ex = (hi >> 20) & 0x7ff;
+    if (ex == 0) return ilogb(v);  // subnormal
+    return ex - 1023;
+}
+
 // z-range of the minor arc x1 -> x2 in FP64: the endpoints' z and, when the
 // arc passes it, the great circle's highest (or lowest) point +-|n_xy| / |n|,
 // widened by 1e-13; false for a degenerate or non-finite arc
