@@ -314,3 +314,55 @@ def ragged_meshes(n_mesh: int, e_min: float, e_max: float, seed: int = DEFAULT_S
             "edge_offsets": edge_offsets,
             "lat_z": np.ascontiguousarray(np.concatenate(Z_parts)),
             "lat_offsets": lat_offsets}
+
+
+# ---------------------------------------------------------- arc x arc pairs --
+def _arc_through(p, d, length, frac):
+    """Endpoints of the arc x(t) = cos t p + sin t d, t in [-frac L, (1 - frac) L]."""
+    t0 = (-frac * length)[:, None]
+    t1 = ((1.0 - frac) * length)[:, None]
+    return np.cos(t0) * p + np.sin(t0) * d, np.cos(t1) * p + np.sin(t1) * d
+
+
+ARC_CLASSES = (("uniform", 0.5), ("short", 0.15), ("parallel", 0.15), ("endpoint", 0.1),
+               ("miss", 0.1))
+
+
+def arc_pairs(n: int, seed: int = DEFAULT_SEED + 5, return_class: bool = False):
+    """Pairs of great circle arcs (a1, a2), (b1, b2) built around a crossing
+    point p: both circles pass through p, at an angle; each arc covers p at a
+    fraction of its length, except for the 'miss' class, whose arc b stops
+    short of p. Classes: 50 % uniform (lengths U(0, pi/2), angle U(0, pi)),
+    15 % short arcs (length log-uniform 1e-10..1e-2 rad), 15 % nearly parallel
+    circles (angle log-uniform 1e-12..1e-3), 10 % crossings near an endpoint
+    (fraction log-uniform 1e-12..1e-3 from either end), 10 % misses."""
+    rng = np.random.default_rng(seed)
+    counts = [int(round(n * w)) for _, w in ARC_CLASSES]
+    counts[0] += n - sum(counts)
+    klass = np.concatenate([np.full(c, i, dtype=np.int8) for i, c in enumerate(counts)])
+    klass = klass[rng.permutation(n)]
+    p = _random_unit(rng, n)
+    d1 = _orthonormal_partner(rng, p)
+    d1x = np.cross(p, d1)
+    ang = rng.uniform(0.0, np.pi, n)
+    par = klass == 2
+    ang[par] = 10.0 ** rng.uniform(-12, -3, par.sum()) * np.where(rng.random(par.sum()) < 0.5, 1, -1)
+    d2 = np.cos(ang)[:, None] * d1 + np.sin(ang)[:, None] * d1x
+    La = rng.uniform(0.0, np.pi / 2, n)
+    Lb = rng.uniform(0.0, np.pi / 2, n)
+    sh = klass == 1
+    La[sh] = 10.0 ** rng.uniform(-10, -2, sh.sum())
+    Lb[sh] = 10.0 ** rng.uniform(-10, -2, sh.sum())
+    fa = rng.random(n)
+    fb = rng.random(n)
+    ep = klass == 3
+    tiny = 10.0 ** rng.uniform(-12, -3, ep.sum())
+    fb[ep] = np.where(rng.random(ep.sum()) < 0.5, tiny, 1.0 - tiny)
+    ms = klass == 4
+    fb[ms] = -rng.uniform(0.05, 1.0, ms.sum())  # arc b ends before reaching p
+    a1, a2 = _arc_through(p, d1, La, fa)
+    b1, b2 = _arc_through(p, d2, Lb, fb)
+    out = tuple(np.ascontiguousarray(v) for v in (a1, a2, b1, b2))
+    if return_class:
+        return out + (klass,)
+    return out
