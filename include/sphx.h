@@ -148,6 +148,25 @@ sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A,
    enqueuing. */
 sphx_status sphx_host_join(sphx_context *ctx, sphx_stream stream);
 
+/* Intersection of two great circle arcs, pair i = (A1[i], A2[i]) and
+   (B1[i], B2[i]): the "three cross products and a normalisation" of Sec. 1
+   (Sec. 9 names it as a use of the accurate cross product). The circles meet
+   at +-v / |v|, v = (a1 x a2) x (b1 x b2); a point is a hit iff it lies on
+   both closed minor arcs, decided as in the latitude call. A1, A2, B1, B2:
+   device, n x 3 row-major FP64, 16-byte aligned. out_pts: device,
+   n x 2 x 3 FP64: slot 0 holds +v / |v|, slot 1 -v / |v|, NaN without a hit.
+   out_count: device, n int32: 0 or 1 (2 only for arcs meeting at both
+   antipodes' boundaries), -1 when an arc's normal is 0 or both arcs lie on
+   one great circle; non-finite inputs give 0. mode: SPHX_MODE_WIDE_INT
+   (integer limbs: the normals exact, v and |v|^2 with 128-bit mantissas,
+   v / |v| rounded to nearest from 96 bits), SPHX_MODE_EFT_FP64 (renormalised
+   AccuDOP normals, each v_i one compensated 6-term dot product, FP64
+   normalisation) or SPHX_MODE_DIRECT_FP64; the others return
+   SPHX_ERR_UNSUPPORTED. Allocates nothing; stream ordered. */
+sphx_status sphx_intersect_gca_gca(const double *A1, const double *A2, const double *B1,
+                                   const double *B2, int64_t n, double *out_pts,
+                                   int32_t *out_count, sphx_mode mode, sphx_stream stream);
+
 /* Candidate latitude ranges of a ragged batch (step a11 of the hot path):
    for each edge e of mesh m, [lo[e], hi[e]) indexes lat_z (global indices)
    and covers every latitude of mesh m inside the edge's z-range (the endpoint

@@ -57,6 +57,8 @@ _SIGS = {
     "sphx_intersect_gca_constlat_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp,
                                                         ctypes.c_int, _vp]),
     "sphx_host_join": (ctypes.c_int, [_vp, _vp]),
+    "sphx_intersect_gca_gca": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
+                                              _vp]),
     "sphx_candidate_ranges": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "sphx_intersect_ragged": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp,
                                              ctypes.c_int, _vp, _i64, _vp, _vp]),
@@ -162,6 +164,19 @@ def sphx_intersect_gca_constlat(A, B, z0, out_pts, out_count, mode="eft", stream
     st = lib().sphx_intersect_gca_constlat(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_pts),
                                            _ptr(out_count), _mode(mode), _stream(stream))
     _check(st, "sphx_intersect_gca_constlat")
+
+
+def sphx_intersect_gca_gca(A1, A2, B1, B2, out_pts, out_count, mode="wide", stream=None):
+    """Intersection of arc (A1[i], A2[i]) with arc (B1[i], B2[i]) (see include/sphx.h):
+    (n, 3) float64 CUDA tensors in, out_pts (n, 2, 3) float64 and out_count (n,) int32."""
+    n = int(A1.shape[0])
+    for t, name in ((A1, "A1"), (A2, "A2"), (B1, "B1"), (B2, "B2")):
+        _dev_tensor(t, torch.float64, name, (n, 3))
+    _dev_tensor(out_pts, torch.float64, "out_pts", (n, 2, 3))
+    _dev_tensor(out_count, torch.int32, "out_count", (n,))
+    st = lib().sphx_intersect_gca_gca(_ptr(A1), _ptr(A2), _ptr(B1), _ptr(B2), n, _ptr(out_pts),
+                                      _ptr(out_count), _mode(mode), _stream(stream))
+    _check(st, "sphx_intersect_gca_gca")
 
 
 def intersect(A, B, z0, mode="eft", stream=None):
