@@ -300,6 +300,7 @@ def main():
     clk = clocks.summary()
     clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
 
+    arcs = arcs_leg(sphx, torch, dev, args, flush) if rank == 0 else None
     ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
     meshes = (meshes_leg(sphx, torch, dev, args, head, mesh_pool)
               if rank == 0 and not args.no_ragged else None)
@@ -359,6 +360,8 @@ def main():
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if arcs is not None:
+        line["arc_x_arc"] = arcs
     if ragged is not None:
         line["ragged_regridding"] = ragged
     if meshes is not None:
@@ -366,6 +369,38 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def arcs_leg(sphx, torch, dev, args, flush) -> dict:
+    """Arc x arc intersections (not the headline): 10^6 pairs of great circle
+    arcs (50 % uniform, 15 % short, 15 % nearly parallel circles, 10 % crossings
+    near an endpoint, 10 % misses), each mode timed with CUDA events over
+    `steps` calls, the L2 cache flushed before each."""
+    A1, A2, B1, B2 = W.arc_pairs(1_000_000)
+    t = [torch.from_numpy(v).to(dev) for v in (A1, A2, B1, B2)]
+    n = len(A1)
+    pts = torch.empty((n, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    cur = torch.cuda.current_stream(dev)
+    res = {"workload": "10^6 arc pairs: 50% uniform, 15% short, 15% nearly parallel, "
+                       "10% crossing near an endpoint, 10% misses", "pairs": n, "modes": {}}
+    for mode in ("wide", "eft", "direct"):
+        ms = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            sphx.sphx_intersect_gca_gca(*t, pts, cnt, mode, cur)
+            e1.record(cur)
+            if i >= args.warmup:
+                ms.append((e0, e1))
+        torch.cuda.synchronize()
+        m = statistics.mean(a.elapsed_time(b) for a, b in ms)
+        res["modes"][mode] = {"ms_per_step": m, "pairs_per_s": n / (m * 1e-3),
+                              "hbm_frac": 148 * n / (m * 1e-3) / 1e9 / measured_hbm_peak()}
+    res["hits"] = int(torch.clamp(cnt, min=0).sum().item())
+    return res
 
 
 def ragged_leg(sphx, torch, dev, args, head) -> dict:
