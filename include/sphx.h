@@ -167,6 +167,16 @@ sphx_status sphx_intersect_gca_gca(const double *A1, const double *A2, const dou
                                    const double *B2, int64_t n, double *out_pts,
                                    int32_t *out_count, sphx_mode mode, sphx_stream stream);
 
+/* The intermediate pairs of Algorithm 8 (SPHX_MODE_EFT_FP64), for the
+   error analysis of App. A: for arc i, 16 doubles at out_mid[16 i]:
+   n[3] and their compensation terms en[3] (AccuDOP), S2, s2 (|n_xy|^2 as a
+   pair), S3, s3 (|n|^2), ss, ess (s^2), sb, es (AccSqrt), X (root 0's
+   x-coordinate numerator, P_x = -X / S2), 0. Quantities past the point where
+   an arc stops (degenerate, no candidate) are 0. Device pointers, layouts as
+   in sphx_intersect_gca_constlat; stream ordered. */
+sphx_status sphx_accux_intermediates(const double *A, const double *B, const double *z0,
+                                     int64_t n, double *out_mid, sphx_stream stream);
+
 /* Candidate latitude ranges of a ragged batch (step a11 of the hot path):
    for each edge e of mesh m, [lo[e], hi[e]) indexes lat_z (global indices)
    and covers every latitude of mesh m inside the edge's z-range (the endpoint

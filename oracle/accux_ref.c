@@ -160,6 +160,7 @@ typedef struct {
     double S2, s2, S3, s3;
     double ss2, ess2; /* [s^2 bar, e] after FastTwoSum */
     double sb, es;    /* AccSqrt */
+    double X;         /* root 0's x-coordinate numerator (CompDot), P_x = -X / S2 */
 } accux_mid;
 
 static int all_finite(const double *a, const double *b, double z0) {
@@ -205,6 +206,7 @@ static void accux_one(const double *x1, const double *x2, double z0, int variant
     fast_two_sum(E, e, &m.ss2, &m.ess2);
     m.sb = 0.0;
     m.es = 0.0;
+    m.X = 0.0;
     if (m.ss2 >= 0.0) acc_sqrt(m.ss2, m.ess2, &m.sb, &m.es);
     if (mid) *mid = m;
 
@@ -245,6 +247,7 @@ static void accux_one(const double *x1, const double *x2, double z0, int variant
     for (int slot = 0; slot < nroots; ++slot) {
         double sg = slot == 0 ? 1.0 : -1.0;
         double xnum = accux_numerator(Fx, eFx, m.n[1], m.en[1], z0, sg * m.sb, sg * m.es);
+        if (mid && slot == 0) mid->X = xnum;
         double ynum = accux_numerator(Fy, eFy, -m.n[0], -m.en[0], z0, sg * m.sb, sg * m.es);
         double Px = -(xnum / m.S2);
         double Py = -(ynum / m.S2);
@@ -343,7 +346,8 @@ void oracle_direct(const double *A, const double *B, const double *z0, int64_t n
 }
 
 /* intermediates of Algorithm 8 (App. A): 16 doubles per arc in the order
-   n[3], en[3], S2, s2, S3, s3, ss2, ess2, sb, es, pad, pad */
+   n[3], en[3], S2, s2, S3, s3, ss2, ess2, sb, es, X, pad (X: root 0's
+   x-coordinate numerator, 0 when the arc has no candidate) */
 void oracle_accux_intermediates(const double *A, const double *B, const double *z0, int64_t n,
                                 int variant, double *mid) {
     for (int64_t i = 0; i < n; ++i) {
@@ -358,7 +362,7 @@ void oracle_accux_intermediates(const double *A, const double *B, const double *
         }
         o[6] = m.S2; o[7] = m.s2; o[8] = m.S3; o[9] = m.s3;
         o[10] = m.ss2; o[11] = m.ess2; o[12] = m.sb; o[13] = m.es;
-        o[14] = 0.0; o[15] = 0.0;
+        o[14] = m.X; o[15] = 0.0;
     }
 }
 

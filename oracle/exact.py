@@ -350,3 +350,25 @@ def intersect_batch(A, B, z0, processes: int | None = None):
         pts[i] = p
         flags[i] = f
     return count, pts, flags
+
+
+# ------------------------------------------------------------ intermediates --
+def intermediates(x1, x2, z0, bits: int = 256):
+    """Exact values of the quantities Algorithm 8 carries (App. A), as Fractions:
+    n (3 components), |n_xy|^2, |n|^2, s^2, s = sqrt(s^2) and the root-0
+    numerator X = z0 n_x n_z + s n_y of the x-coordinate (P_x = -X / |n_xy|^2).
+    s and X are irrational: they are given to within 2^-bits relative."""
+    ex = setup(tuple(float(v) for v in x1), tuple(float(v) for v in x2), float(z0))
+    n = [Fraction(v) * Fraction(2) ** (2 * ex.E) for v in ex.N]
+    S2 = n[0] ** 2 + n[1] ** 2
+    S3 = S2 + n[2] ** 2
+    z = Fraction(float(z0))
+    Q = S2 - S3 * z * z
+    s = None
+    if Q >= 0:
+        num, den = Q.numerator, Q.denominator
+        k = bits + max(0, den.bit_length() - num.bit_length())
+        r = math.isqrt((num << (2 * k)) // den)  # sqrt(Q) 2^k, truncated
+        s = Fraction(r, 1 << k)
+    X = z * n[0] * n[2] + s * n[1] if s is not None else None
+    return {"n": n, "S2": S2, "S3": S3, "Q": Q, "s": s, "X": X}

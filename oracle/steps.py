@@ -96,7 +96,7 @@ def accux_intermediates(A, B, z0, variant: int = 0):
     lib().oracle_accux_intermediates(pa, pb, pz, n, variant, _d(mid)[1])
     return {"n": mid[:, 0:3], "en": mid[:, 3:6], "S2": mid[:, 6], "s2": mid[:, 7],
             "S3": mid[:, 8], "s3": mid[:, 9], "ss2": mid[:, 10], "ess2": mid[:, 11],
-            "sb": mid[:, 12], "es": mid[:, 13]}
+            "sb": mid[:, 12], "es": mid[:, 13], "X": mid[:, 14], "raw": mid}
 
 
 def _pair_out(n):

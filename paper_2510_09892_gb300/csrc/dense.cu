@@ -148,3 +148,33 @@ extern "C" sphx_status sphx_intersect_gca_constlat(const double *A, const double
     }
     return SPHX_OK;
 }
+
+namespace sphx {
+__global__ void accux_mid_kernel(const double *__restrict__ A, const double *__restrict__ B,
+                                 const double *__restrict__ Z, int64_t n, double *__restrict__ mid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
+        const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        PairOut o;
+        pair_accux<true>(x1, x2, Z[i], o, mid + 16 * i);
+    }
+}
+}  // namespace sphx
+
+extern "C" sphx_status sphx_accux_intermediates(const double *A, const double *B,
+                                                const double *z0, int64_t n, double *out_mid,
+                                                sphx_stream stream) {
+    if (n < 0) return SPHX_ERR_INVALID_ARG;
+    if (n == 0) return SPHX_OK;
+    if (!A || !B || !z0 || !out_mid) return SPHX_ERR_INVALID_ARG;
+    const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 16);
+    accux_mid_kernel<<<(unsigned)blocks, 128, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        A, B, z0, n, out_mid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return SPHX_ERR_CUDA;
+    }
+    return SPHX_OK;
+}

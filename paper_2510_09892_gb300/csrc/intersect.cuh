@@ -84,9 +84,16 @@ __device__ __forceinline__ void pair_direct(const double (&x1)[3], const double 
 }
 
 // ---- Algorithm 8 (AccuX) in FP64, both roots --------------------------------
+// mid (optional): Algorithm 8's pairs for the intermediate-error analysis of
+// App. A, 16 doubles: n[3], en[3], S2, s2, S3, s3, ss, ess, sb, es, X (root
+// 0's x-coordinate numerator), 0 -- zeros past the point where the arc stops
 template <bool Renorm>
 __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (&x2)[3],
-                                           double z0, PairOut &o) {
+                                           double z0, PairOut &o, double *mid = nullptr) {
+    if (mid) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) mid[k] = 0.0;
+    }
     if (!finite7(x1, x2, z0)) return clear(o, 0);
     // n = x1 x x2 as three compensated pairs
     double n[3], en[3];
@@ -98,6 +105,17 @@ __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (
         const double nxy[2] = {n[0], n[1]}, exy[2] = {en[0], en[1]};
         sum_of_squares_c<double, 2>(nxy, exy, S2, s2);
         sum_of_squares_c<double, 3>(n, en, S3, s3);
+    }
+    if (mid) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mid[k] = n[k];
+            mid[3 + k] = en[k];
+        }
+        mid[6] = S2;
+        mid[7] = s2;
+        mid[8] = S3;
+        mid[9] = s3;
     }
     if (S3 == 0.0) return clear(o, -1);
     if (S2 == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
@@ -112,9 +130,17 @@ __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (
     double e = add(sub(s2, eD), eE);
     double ss, ess;
     fast_two_sum(E, e, ss, ess);
+    if (mid) {
+        mid[10] = ss;
+        mid[11] = ess;
+    }
     if (!(ss >= 0.0)) return clear(o, 0);
     double sb, es;
     acc_sqrt(ss, ess, sb, es);
+    if (mid) {
+        mid[12] = sb;
+        mid[13] = es;
+    }
     // F = n_x n_z and n_y n_z with their first-order compensation terms
     double Fx, eFx, Fy, eFy;
     two_prod(n[0], n[2], Fx, eFx);
@@ -141,6 +167,7 @@ __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (
         const double xb[6] = {Fy, eFy, -n[0], -en[0], -n[0], -en[0]};
         double X = comp_dot<double, 6>(xa, yy);
         double Y = comp_dot<double, 6>(xb, yy);
+        if (mid && r == 0) mid[14] = X;
         double Px = -div_(X, S2);
         double Py = -div_(Y, S2);
         double t1 = fma_(Px, m1x, fma_(Py, m1y, mul(z0, m1z)));

@@ -57,6 +57,7 @@ _SIGS = {
     "sphx_intersect_gca_constlat_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp,
                                                         ctypes.c_int, _vp]),
     "sphx_host_join": (ctypes.c_int, [_vp, _vp]),
+    "sphx_accux_intermediates": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "sphx_intersect_gca_gca": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int,
                                               _vp]),
     "sphx_candidate_ranges": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
@@ -177,6 +178,15 @@ def sphx_intersect_gca_gca(A1, A2, B1, B2, out_pts, out_count, mode="wide", stre
     st = lib().sphx_intersect_gca_gca(_ptr(A1), _ptr(A2), _ptr(B1), _ptr(B2), n, _ptr(out_pts),
                                       _ptr(out_count), _mode(mode), _stream(stream))
     _check(st, "sphx_intersect_gca_gca")
+
+
+def sphx_accux_intermediates(A, B, z0, out_mid, stream=None):
+    """Algorithm 8's intermediate pairs per arc (App. A): out_mid (n, 16) float64."""
+    n = int(z0.shape[0])
+    _dev_tensor(out_mid, torch.float64, "out_mid", (n, 16))
+    st = lib().sphx_accux_intermediates(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_mid),
+                                        _stream(stream))
+    _check(st, "sphx_accux_intermediates")
 
 
 def intersect(A, B, z0, mode="eft", stream=None):

@@ -302,3 +302,38 @@ def test_host_buffer_calls_overlap_and_join():
     for (cnt, pts), (_, _, _, hP, hC) in zip(want, outs):
         assert np.array_equal(hC.numpy(), cnt)
         assert P.same_bits(hP.numpy(), pts)
+
+
+def test_accux_intermediates_equal_step_reference():
+    """sphx_accux_intermediates (App. A) dumps exactly the pairs the step
+    reference carries, for every arc with a candidate."""
+    A, B, z = W.uniform_arcs(20_000, seed=71)
+    dev = torch.device("cuda:0")
+    tA, tB, tz = (torch.from_numpy(v).to(dev) for v in (A, B, z))
+    mid = torch.empty((len(z), 16), dtype=torch.float64, device=dev)
+    sphx.sphx_accux_intermediates(tA, tB, tz, mid)
+    torch.cuda.synchronize()
+    g = mid.cpu().numpy()
+    r = steps.accux_intermediates(A, B, z, variant=2)["raw"]
+    ok = r[:, 10] >= 0  # arcs with candidates (s^2 >= 0): the whole chain ran
+    assert P.same_bits(g[ok, :15], r[ok, :15])
+
+
+@pytest.mark.parametrize("mode", ["wide", "eft", "direct", "ff32"])
+@pytest.mark.parametrize("axis", [0, 1, 2, "swap"])
+def test_reflection_equivariance_on_gpu(mode, axis):
+    """Reflected inputs give the reflected outputs bit for bit (slots exchanged
+    where the s-term of Eq. 2.2 changes sign): the reduction of Sec. 3 holds
+    exactly for every mode, except the endpoint swap for float-float, whose
+    x1 x (x2 -+ x1) is not symmetric in the endpoints."""
+    if mode == "ff32" and axis == "swap":
+        pytest.skip("float-float forms x1 x (x2 -+ x1): not swap-symmetric")
+    from tests.test_oracle_steps import _reflect, equal_as_mapped, expected_after
+    A, B, z = W.stress_arcs(20_000, seed=72)
+    c0, p0 = run(A, B, z, mode)
+    if axis == "swap":
+        c1, p1 = run(B, A, z, mode)
+    else:
+        c1, p1 = run(*_reflect(A, B, z, axis), mode)
+    assert np.array_equal(c0, c1)
+    assert equal_as_mapped(c0, p1, expected_after(p0, axis))

@@ -193,3 +193,106 @@ def test_direct_obeys_section4_bound():
     ok = (fl == 0) & (c == cnt)
     assert (err[ok] <= 1.5 * bound[ok][:, None]).all()
     assert err[ok].max() > 10  # and it is visibly worse than AccuX
+
+
+# ---- App. A: intermediate errors; the reflection assumption of Sec. 3 --------
+def test_exact_intermediates_give_the_pinned_point():
+    """-X / |n_xy|^2 from oracle.exact.intermediates rounds to the oracle's
+    (independently rounded, pinned) slot-0 candidate."""
+    A, B, z = W.uniform_arcs(300, seed=301)
+    for i in range(300):
+        it = exact.intermediates(A[i], B[i], z[i])
+        ex = exact.setup(tuple(A[i]), tuple(B[i]), float(z[i]))
+        if it["s"] is None or ex.S2i == 0:
+            continue
+        px = exact.candidate_point(ex, 1)[0]
+        val = -it["X"] / it["S2"]
+        assert abs(float(val) - px) <= 2.0 ** -52 * max(abs(px), 2.0 ** -60)
+
+
+def test_app_a_intermediates_below_u_until_the_final_roundings():
+    """App. A: averaged over the primary-dataset stand-in, every pair that
+    Algorithm 8 carries (n, |n_xy|^2, |n|^2, s^2, s, the numerator) has a
+    relative error below u; only the final single-double roundings reach ~u."""
+    A, B, z = W.uniform_arcs(600, seed=302)
+    mid = steps.accux_intermediates(A, B, z, variant=2)
+    errs = {k: [] for k in ("n", "S2", "S3", "Q", "s", "X", "fl_S2", "fl_X")}
+    for i in range(600):
+        it = exact.intermediates(A[i], B[i], z[i])
+        if it["s"] is None or it["Q"] == 0 or it["X"] == 0:
+            continue
+
+        def rel(pair_hi, pair_lo, ref):
+            return abs(float((Fr(pair_hi) + Fr(pair_lo) - ref) / ref))
+        for k in range(3):
+            if it["n"][k] != 0:
+                errs["n"].append(rel(mid["n"][i, k], mid["en"][i, k], it["n"][k]))
+        errs["S2"].append(rel(mid["S2"][i], mid["s2"][i], it["S2"]))
+        errs["S3"].append(rel(mid["S3"][i], mid["s3"][i], it["S3"]))
+        errs["Q"].append(rel(mid["ss2"][i], mid["ess2"][i], it["Q"]))
+        errs["s"].append(rel(mid["sb"][i], mid["es"][i], it["s"]))
+        errs["X"].append(rel(mid["X"][i], 0.0, it["X"]))
+        errs["fl_S2"].append(rel(mid["S2"][i], 0.0, it["S2"]))
+        errs["fl_X"].append(rel(mid["X"][i], 0.0, it["X"]))
+    mean = {k: float(np.mean(v)) for k, v in errs.items()}
+    for k in ("n", "S2", "S3", "Q", "s"):
+        assert mean[k] < 2.0 ** -80, (k, mean[k])   # pairs: O(u^2), far below u
+    for k in ("X", "fl_S2", "fl_X"):
+        assert mean[k] < U, (k, mean[k])             # single doubles: below u on average
+
+
+def _reflect(A, B, z, axis):
+    A2, B2, z2 = A.copy(), B.copy(), z.copy()
+    A2[:, axis] = -A2[:, axis]
+    B2[:, axis] = -B2[:, axis]
+    if axis == 2:
+        z2 = -z2
+    return A2, B2, z2
+
+
+def expected_after(pts, axis):
+    """Points of the original arcs mapped by a reflection (axis 0, 1, 2) or an
+    endpoint swap ('swap'): coordinate signs and, where the sign of the s-term
+    of Eq. 2.2 flips (z reflection, swap), the two slots exchanged."""
+    out = pts.copy()
+    if axis in (0, 1):
+        out[..., axis] = -out[..., axis]
+        return out
+    out = out[:, ::-1, :].copy()
+    if axis == 2:
+        out[..., 2] = -out[..., 2]
+    return out
+
+
+def equal_as_mapped(c, got, want):
+    """Bitwise equality of mapped outputs: two-hit arcs slot by slot, one-hit
+    arcs by their point (a tangent point is always reported in slot 0, so a
+    slot-exchanging map leaves it there), no-hit arcs all NaN."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    two = c == 2
+    if not np.array_equal(got[two].view(np.int64), want[two].view(np.int64)):
+        return False
+    for i in np.flatnonzero(c == 1):
+        g = got[i][np.isfinite(got[i, :, 0])]
+        w = want[i][np.isfinite(want[i, :, 0])]
+        if g.shape != (1, 3) or not np.array_equal(g.view(np.int64), w.view(np.int64)):
+            return False
+    return bool(np.isnan(got[c <= 0]).all() and np.isnan(want[c <= 0]).all())
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2, "swap"])
+def test_step_reference_is_reflection_equivariant(axis):
+    """Sec. 3 reduces the analysis to n >= 0, z0 >= 0 by reflections "without
+    loss of generality". In round-to-nearest arithmetic every step of
+    Algorithm 8 (and of the direct form) commutes with negations and
+    operand swaps, so the reduction holds bit for bit."""
+    A, B, z = W.stress_arcs(4000, seed=303)
+    for fn in (lambda a, b, c: steps.accux(a, b, c, variant=2), steps.direct):
+        c0, p0 = fn(A, B, z)
+        if axis == "swap":
+            c1, p1 = fn(B, A, z)
+        else:
+            c1, p1 = fn(*_reflect(A, B, z, axis))
+        assert np.array_equal(c0, c1)
+        assert equal_as_mapped(c0, p1, expected_after(p0, axis))
