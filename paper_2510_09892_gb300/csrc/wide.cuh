@@ -212,6 +212,12 @@ SPHX_HD W<K> negate(W<K> a) {
 // m >>= d (d >= 0), truncating
 template <int K>
 SPHX_HD void shr(uint32_t (&m)[K], int d) {
+    if (d < 32) {  // the common alignment: funnel shifts only
+#pragma unroll
+        for (int i = 0; i < K - 1; ++i) m[i] = funnel_r(m[i], m[i + 1], d);
+        m[K - 1] = d ? (m[K - 1] >> d) : m[K - 1];
+        return;
+    }
     if (d >= 32 * K) {
 #pragma unroll
         for (int i = 0; i < K; ++i) m[i] = 0u;
