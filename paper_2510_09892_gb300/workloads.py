@@ -24,6 +24,8 @@ for them with the same structure:
 * ``cubed_sphere_edges`` + ``latlon_latitudes`` the regridding workload.
 * ``ragged_meshes``   independent random polygon meshes with per-mesh
                       latitude grids.
+* ``cubed_sphere_cells`` / ``polygon_cells``  node-indexed cells (counter-
+                      clockwise seen from outside) for the band-area step.
 """
 from __future__ import annotations
 
@@ -365,4 +367,94 @@ def arc_pairs(n: int, seed: int = DEFAULT_SEED + 5, return_class: bool = False):
     out = tuple(np.ascontiguousarray(v) for v in (a1, a2, b1, b2))
     if return_class:
         return out + (klass,)
+    return out
+
+
+# ---- node-indexed cells for the band-area (zonal-mean) step -------------------
+def _tan_grid(N: int):
+    """tan of N + 1 equiangular angles from -pi/4 to pi/4, odd-symmetric, with
+    exact ends: T[0] = -1, T[N] = 1, T[N - i] = -T[i]."""
+    t = np.tan(-np.pi / 4 + (np.pi / 2) * np.arange(N + 1) / N)
+    half = (N + 1) // 2
+    t[N + 1 - half:] = -t[:half][::-1]
+    if N % 2 == 0:
+        t[N // 2] = 0.0
+    t[0], t[N] = -1.0, 1.0
+    return t
+
+
+def cubed_sphere_cells(N: int):
+    """Equiangular gnomonic cubed sphere as node-indexed quadrilaterals.
+
+    Every node is a point (T[i], T[j], T[k]) of the cube surface's lattice
+    (i, j, k in 0..N, one of them 0 or N), normalised; a node shared by
+    several faces of the cube is stored once, so neighbouring cells share
+    their edges bit for bit. Cells run counter-clockwise seen from outside.
+    For even N the poles are nodes; for odd N each pole lies inside a cell.
+
+    Returns (nodes (6 N^2 + 2, 3) float64, face_offsets (6 N^2 + 1,) int64,
+    face_nodes (24 N^2,) int32).
+    """
+    T = _tan_grid(N)
+    n1 = N + 1
+    a, b = np.meshgrid(np.arange(n1), np.arange(n1), indexing="ij")
+    full = np.full_like(a, N)
+    zero = np.zeros_like(a)
+    # (i, j, k) lattice indices per cube face, with in-face axes u, v such that
+    # u x v is the outward normal (so increasing (u, v) order is counter-clockwise)
+    faces = [(full, a, b),   # +x: u = y, v = z
+             (zero, b, a),   # -x: u = z, v = y
+             (b, full, a),   # +y: u = z, v = x
+             (a, zero, b),   # -y: u = x, v = z
+             (a, b, full),   # +z: u = x, v = y
+             (b, a, zero)]   # -z: u = y, v = x
+    keys = np.concatenate([((i * n1 + j) * n1 + k).ravel() for i, j, k in faces])
+    uniq, inv = np.unique(keys, return_inverse=True)
+    ii, rem = np.divmod(uniq, n1 * n1)
+    jj, kk = np.divmod(rem, n1)
+    P = np.stack([T[ii], T[jj], T[kk]], axis=1)
+    nodes = np.ascontiguousarray(P / np.sqrt(np.sum(P * P, axis=1, keepdims=True)))
+    inv = inv.reshape(6, n1, n1).astype(np.int32)
+    quads = np.stack([inv[:, :-1, :-1], inv[:, 1:, :-1], inv[:, 1:, 1:], inv[:, :-1, 1:]],
+                     axis=-1)
+    face_nodes = np.ascontiguousarray(quads.reshape(-1))
+    face_offsets = 4 * np.arange(6 * N * N + 1, dtype=np.int64)
+    return nodes, face_offsets, face_nodes
+
+
+def polygon_cells(n_cells: int, seed: int = DEFAULT_SEED + 6, radius=(1e-3, 0.3),
+                  kmin: int = 3, kmax: int = 12, star: float = 0.3):
+    """Independent random star-shaped polygons (kmin..kmax vertices), centres
+    uniform on the sphere, radius log-uniform in [radius], vertex radii
+    jittered by +-star (non-convex for star > 0), counter-clockwise.
+
+    Returns (nodes, face_offsets, face_nodes) like ``cubed_sphere_cells``
+    (each cell owns its nodes).
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7]))
+    c = _random_unit(rng, n_cells)
+    e1 = _orthonormal_partner(rng, c)
+    e2 = np.cross(c, e1)  # e1 x e2 = c: increasing angle is counter-clockwise
+    k = rng.integers(kmin, kmax + 1, n_cells)
+    rad = np.exp(rng.uniform(math.log(radius[0]), math.log(radius[1]), n_cells))
+    tot = int(k.sum())
+    cell = np.repeat(np.arange(n_cells), k)
+    first = np.concatenate([[0], np.cumsum(k)[:-1]])
+    j = np.arange(tot) - first[cell]
+    ang = 2 * np.pi * (j + 0.4 * rng.random(tot)) / k[cell]
+    r = rad[cell] * (1.0 + star * rng.uniform(-1.0, 1.0, tot))
+    V = c[cell] + np.tan(r)[:, None] * (np.cos(ang)[:, None] * e1[cell] +
+                                        np.sin(ang)[:, None] * e2[cell])
+    nodes = np.ascontiguousarray(_unit(V))
+    face_offsets = np.concatenate([[0], np.cumsum(k)]).astype(np.int64)
+    return nodes, face_offsets, np.arange(tot, dtype=np.int32)
+
+
+def cells_as_lists(nodes, face_offsets, face_nodes, which=None):
+    """Cells as lists of vertex tuples (for the oracle), optionally a subset."""
+    idx = range(len(face_offsets) - 1) if which is None else which
+    out = []
+    for f in idx:
+        ids = face_nodes[face_offsets[f]:face_offsets[f + 1]]
+        out.append([tuple(float(x) for x in nodes[i]) for i in ids])
     return out
