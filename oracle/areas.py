@@ -95,6 +95,8 @@ def winding(cell) -> int:
     m = len(cell)
     for i in range(m):
         a, b = cell[i], cell[(i + 1) % m]
+        if (float(a[0]) == 0.0 and float(a[1]) == 0.0) or (float(b[0]) == 0.0 and float(b[1]) == 0.0):
+            continue  # a pole has no longitude: an arc from or to it steps none
         cr = float(a[0]) * float(b[1]) - float(a[1]) * float(b[0])
         dt = float(a[0]) * float(b[0]) + float(a[1]) * float(b[1])
         tot += math.atan2(cr, dt)
