@@ -213,6 +213,77 @@ sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const doub
                                   sphx_mode mode, sphx_hit *out, int64_t out_cap,
                                   int64_t *out_total, sphx_stream stream);
 
+/* ---- band areas of spherical cells (the zonal-mean step) -----------------
+   Sec. 1 names zonal means as the use that makes arc-latitude intersections
+   matter; the paper gives no algorithm for this step, so these calls are this
+   library's design around its intersections.
+
+   Mesh arguments, shared by the three calls below:
+     nodes         device, n_nodes x 3 FP64 (row-major): node directions, any
+                   nonzero length;
+     face_offsets  device int64[n_faces + 1]: cell f is the node list
+                   face_nodes[face_offsets[f] .. face_offsets[f + 1]);
+     face_nodes    device int32[n_face_nodes]: node indices.
+   A cell is a simple spherical polygon whose consecutive nodes (and the last
+   and the first) are joined by minor great circle arcs, counter-clockwise
+   seen from outside the sphere, with at most one pole in its interior (a pole
+   may be a node). lat_z: device, n_lat >= 2 FP64, strictly ascending, in
+   [-1, 1]; band k (0 <= k < n_lat - 1) is z_k <= z <= z_{k+1}. Parts of a
+   cell outside [z_0, z_{n_lat-1}] are in no band. Cells whose offsets or node
+   indices fall outside these arrays get no bands, and sphx_sync_status()
+   reports SPHX_ERR_INVALID_ARG. */
+
+/* Bands each cell can meet: band_lo[f] <= k < band_hi[f] (device int32[n_faces]
+   each), from the cell's height range (arc endpoints and, where an arc passes
+   it, its highest or lowest point, widened by 1e-13; up to the pole for a cell
+   around a pole), and area_offsets (device int64[n_faces + 1]), the exclusive
+   prefix sum of band_hi - band_lo: the area of cell f in band k goes to
+   areas[area_offsets[f] + k - band_lo[f]], and area_offsets[n_faces] is the
+   number of entries. Scratch for the prefix sum comes from ctx. Stream
+   ordered. */
+sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+                             const int64_t *face_offsets, const int32_t *face_nodes,
+                             int64_t n_face_nodes, int64_t n_faces, const double *lat_z,
+                             int64_t n_lat, int32_t *band_lo, int32_t *band_hi,
+                             int64_t *area_offsets, sphx_stream stream);
+
+/* Area of every cell in every band of its range (layout of sphx_band_ranges;
+   areas: device FP64[areas_cap]). Each arc is cut where it crosses the
+   latitudes in its height range, the crossings computed by `mode` as in
+   sphx_intersect_gca_constlat (Eq. 2.2: slot 0 crosses upwards along the
+   arc, slot 1 downwards). In longitude and height the area element is
+   dlambda dz, so a region's area is the boundary integral of lambda dz (Green);
+   the latitude pieces of the boundary have dz = 0, and every arc piece adds
+   [lambda z] minus the integral of z dlambda along it (the signed area between
+   the piece and the equator, in closed form) to the band it lies in, lambda
+   unwrapped along the cell from its first node off the poles. A cell around a
+   pole adds 2 pi times each band's share of the height between that node and
+   the pole. Areas are FP64 with an absolute error of a few units of rounding
+   times (the sum over the cell's arcs of their longitude spans plus the
+   cell's height range). Entries past
+   areas_cap are not written (sphx_sync_status() reports SPHX_ERR_CAPACITY).
+   mode: any sphx_mode. Stream ordered; allocates nothing. */
+sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+                            const int64_t *face_offsets, const int32_t *face_nodes,
+                            int64_t n_face_nodes, int64_t n_faces, const double *lat_z,
+                            int64_t n_lat, const int32_t *band_lo, const int32_t *band_hi,
+                            const int64_t *area_offsets, sphx_mode mode, double *areas,
+                            int64_t areas_cap, sphx_stream stream);
+
+/* Zonal sums: for every band k, out_fa[k] = sum over cells of field[f] *
+   A[f, k] and out_a[k] = sum of A[f, k] (device FP64[n_lat - 1] each); the
+   zonal mean is out_fa / out_a. field: device FP64[n_faces]. Each term is
+   rounded once to a multiple of 2^-80 and summed exactly in 128-bit fixed
+   point, so the sums do not depend on the order the GPU adds them in
+   (bitwise reproducible); the results are the exact sums rounded to FP64.
+   Terms of magnitude 2^46 or more, or non-finite, are left out and
+   sphx_sync_status() reports SPHX_ERR_INVALID_ARG. Scratch comes from ctx.
+   Stream ordered. */
+sphx_status sphx_zonal_sums(sphx_context *ctx, const int32_t *band_lo, const int32_t *band_hi,
+                            const int64_t *area_offsets, int64_t n_faces, const double *areas,
+                            const double *field, int64_t n_lat, double *out_fa, double *out_a,
+                            sphx_stream stream);
+
 /* Largest edge count sphx_intersect_ragged_noalloc accepts. */
 #define SPHX_NOALLOC_MAX_EDGES 262144
 

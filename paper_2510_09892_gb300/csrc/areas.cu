@@ -1,0 +1,628 @@
+// Band areas of spherical cells and zonal sums: the zonal-mean step that
+// Sec. 1 names as the use of arc-latitude intersections.
+//
+//  1. band_range_kernel  one thread per cell: the height range of its arcs
+//                        (ranges.cuh) and its winding number around the
+//                        z-axis give the bands [lo, hi) it can meet; the
+//                        ragged call's prefix sum turns the counts into
+//                        output offsets.
+//  2. band_area_kernel   one thread per cell. In longitude and height the
+//                        area element is dlambda dz, so by Green's theorem a
+//                        region's area is the boundary integral of lambda dz.
+//                        The boundary of (cell ∩ band) consists of arc pieces
+//                        and latitude pieces; the latter have dz = 0. So each
+//                        arc is cut at its crossings with the latitudes
+//                        (Eq. 2.2, evaluated by the chosen mode), and every
+//                        piece p -> q adds
+//                            lambda_q z_q - lambda_p z_p - T(p, q)
+//                        to the band it lies in, where T(p, q), the integral
+//                        of z dlambda along the piece, is the signed area
+//                        between the piece and the equator:
+//                            T = 2 atan2(sin(dl/2) (t_p + t_q),
+//                                        cos(dl/2) (1 + t_p t_q)),
+//                        t = tan(latitude / 2) = z / (1 + rho), with the
+//                        half-angle ratio tan(dl/2) = cr / (rho_p rho_q + dt)
+//                        from the pieces' xy cross and dot products.
+//                        lambda is unwrapped along the cell from its first
+//                        node off the poles (lambda = 0 there); a cell around
+//                        a pole (winding +-1) needs a cut from that node to
+//                        the pole, across which lambda jumps by 2 pi: it adds
+//                        2 pi times each band's share of the cut's height.
+//                        Crossings come in order along the arc without a
+//                        sort: slot 0 of Eq. 2.2 crosses upwards along the
+//                        arc and slot 1 downwards, so a rising run takes the
+//                        slot-0 hits of ascending latitudes and a falling run
+//                        the slot-1 hits of descending ones, an arc that
+//                        passes its highest (lowest) point being split there
+//                        into a rising and a falling run.
+//  3. zonal_sum_kernel   per band, sum of field * area and of area, in 128-bit
+//                        fixed point with 64-bit integer atomics (per block in
+//                        shared memory, then once per block in global memory),
+//                        so the result does not depend on the order of the
+//                        additions.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "intersect.cuh"
+#include "ranges.cuh"
+
+namespace sphx {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kAreaThreads = 128;
+constexpr int64_t kSmemLat = 4096;  // latitudes staged in shared memory up to this count
+constexpr int kFracBits = 80;       // zonal sums: fixed point with 2^-80 resolution
+constexpr int kZonalThreads = 256;
+constexpr int64_t kSmemBands = 3072;  // bands accumulated in shared memory up to this count
+// a point this close to the z-axis (|xy| < 2^-40) counts as a pole: its
+// computed longitude would be rounding noise
+constexpr double kPoleRho = 9.094947017729282e-13;
+
+struct Mesh {
+    const double *nodes;
+    int64_t n_nodes;
+    const int64_t *face_offsets;
+    const int32_t *face_nodes;
+    int64_t n_face_nodes, n_faces;
+    const double *lat;
+    int64_t L;
+    unsigned *status;
+};
+
+// node range [s, e) of cell f in face_nodes; false (status flagged) if invalid
+__device__ __forceinline__ bool cell_span(const Mesh &m, int64_t f, int64_t &s, int64_t &e) {
+    s = m.face_offsets[f];
+    e = m.face_offsets[f + 1];
+    if (s < 0 || e < s || e > m.n_face_nodes) {
+        atomicOr(m.status, kStatusInvalid);
+        return false;
+    }
+    return true;
+}
+
+// coordinates of node face_nodes[i]; false (status flagged) for an index
+// outside the node array
+__device__ __forceinline__ bool node_at(const Mesh &m, int64_t i, double (&v)[3]) {
+    const int32_t id = m.face_nodes[i];
+    if (id < 0 || (int64_t)id >= m.n_nodes) {
+        atomicOr(m.status, kStatusInvalid);
+        return false;
+    }
+    const double *p = m.nodes + 3 * (int64_t)id;
+    v[0] = p[0];
+    v[1] = p[1];
+    v[2] = p[2];
+    return true;
+}
+
+__device__ __forceinline__ void unit(const double (&v)[3], double (&u)[3]) {
+    const double r = 1.0 / sqrt(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
+    u[0] = v[0] * r;
+    u[1] = v[1] * r;
+    u[2] = v[2] * r;
+}
+
+// a point of an arc with what the boundary integral needs
+struct Pt {
+    double x, y, z;  // unit vector
+    double rho;      // sqrt(x^2 + y^2)
+    double t;        // tan(latitude / 2) = z / (1 + rho)
+    double d;        // longitude from the arc's reference meridian, in [-pi, pi]
+};                   // (rho = 0 and no longitude at a pole)
+
+// angle from the meridian of unit vector r to that of unit vector p (xy
+// parts): the cross product from the differences p - r, r x p = r x (p - r),
+// so that a small angle comes out accurate relative to itself (the plain
+// products would leave an absolute error of a unit of rounding)
+__device__ __forceinline__ double delta_lon(double rx, double ry, double x, double y) {
+    return atan2(rx * (y - ry) - ry * (x - rx), fma(rx, x, ry * y));
+}
+
+__device__ __forceinline__ Pt make_pt(double x, double y, double z, double rx, double ry) {
+    Pt p;
+    p.x = x;
+    p.y = y;
+    p.z = z;
+    p.rho = sqrt(fma(x, x, y * y));
+    if (p.rho < kPoleRho) {
+        p.x = p.y = p.rho = p.d = 0.0;
+        p.t = z;
+        return p;
+    }
+    p.t = z / (1.0 + p.rho);
+    p.d = delta_lon(rx, ry, x, y);
+    return p;
+}
+
+// piece p -> q of an arc whose longitudes are lam + d: add
+// lambda_q z_q - lambda_p z_p - T(p, q) to the band holding the piece's
+// midpoint. A piece from or to a pole runs along a meridian: lambda is the
+// other end's all along it and T = 0.
+__device__ __forceinline__ void add_piece(const Pt &p, const Pt &q, double lam, const double *lat,
+                                          int64_t L, int64_t klo, int64_t nb, double *out) {
+    const bool p_pole = p.rho == 0.0, q_pole = q.rho == 0.0;
+    if (p_pole && q_pole) return;
+    const double sx = p.x + q.x, sy = p.y + q.y, sz = p.z + q.z;
+    const double zm = sz / sqrt(fma(sx, sx, fma(sy, sy, sz * sz)));
+    const int64_t k = upper_bound_ord(lat, L, ord64(zm)) - 1;
+    if (k < klo || k >= klo + nb) return;
+    double T = 0.0;
+    if (!(p_pole || q_pole)) {
+        const double cr = p.x * (q.y - p.y) - p.y * (q.x - p.x);  // as in delta_lon
+        const double dt = fma(p.rho, q.rho, fma(p.x, q.x, p.y * q.y));
+        T = 2.0 * atan2(cr * (p.t + q.t), dt * fma(p.t, q.t, 1.0));
+    }
+    const double pd = p_pole ? q.d : p.d, qd = q_pole ? p.d : q.d;
+    const double I = fma(lam, q.z - p.z, fma(qd, q.z, -pd * p.z)) - T;
+    out[k - klo] += I;
+}
+
+// all pieces of the arc a -> b (raw a, b for Eq. 2.2; ua, ub of unit length),
+// longitudes lam + (angle from (rx, ry))
+template <int Mode>
+__device__ __forceinline__ void arc_pieces(const double (&a)[3], const double (&b)[3],
+                                           const double (&ua)[3], const double (&ub)[3],
+                                           double rx, double ry, double lam, const double *lat,
+                                           int64_t L, int64_t klo, int64_t nb, double *out) {
+    const double nx = ua[1] * ub[2] - ua[2] * ub[1];
+    const double ny = ua[2] * ub[0] - ua[0] * ub[2];
+    const double nz = ua[0] * ub[1] - ua[1] * ub[0];
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) return;
+    // (n x x)_z, the vertical direction of travel at x: > 0 where the arc rises
+    const double ga = nx * ua[1] - ny * ua[0];
+    const double gb = nx * ub[1] - ny * ub[0];
+    Pt ends[3];
+    bool ups[2];
+    int nruns;
+    ends[0] = make_pt(ua[0], ua[1], ua[2], rx, ry);
+    if ((ga > 0.0 && gb < 0.0) || (ga < 0.0 && gb > 0.0)) {
+        // the arc passes the great circle's highest point (rises, then falls)
+        // or its lowest; the highest is (-nx nz, -ny nz, nx^2 + ny^2) / (|n| |n_xy|)
+        const double S2 = fma(nx, nx, ny * ny);
+        const double sc = (ga > 0.0 ? 1.0 : -1.0) / (sqrt(fma(nz, nz, S2)) * sqrt(S2));
+        ends[1] = make_pt(-nx * nz * sc, -ny * nz * sc, S2 * sc, rx, ry);
+        ends[2] = make_pt(ub[0], ub[1], ub[2], rx, ry);
+        ups[0] = ga > 0.0;
+        ups[1] = !ups[0];
+        nruns = 2;
+    } else {
+        ends[1] = make_pt(ub[0], ub[1], ub[2], rx, ry);
+        ups[0] = ub[2] >= ua[2];
+        ups[1] = false;
+        nruns = 1;
+    }
+    for (int r = 0; r < nruns; ++r) {
+        const bool up = ups[r];
+        const Pt p1 = ends[r + 1];
+        const double zl = fmin(ends[r].z, p1.z) - kZWiden, zh = fmax(ends[r].z, p1.z) + kZWiden;
+        const int64_t j0 = lower_bound_ord(lat, L, ord64(zl));
+        const int64_t j1 = upper_bound_ord(lat, L, ord64(zh));
+        const int64_t cnt = j1 > j0 ? j1 - j0 : 0;
+        const int slot = up ? 0 : 1;
+        Pt prev = ends[r];
+        for (int64_t i = 0; i <= cnt; ++i) {
+            Pt q;
+            if (i < cnt) {
+                const int64_t j = up ? j0 + i : j1 - 1 - i;
+                const double z0 = lat[j];
+                PairOut o;
+                intersect_pair<Mode>(a, b, z0, o);
+                if (!(o.count > 0 && o.hit[slot])) continue;
+                q = make_pt(o.px[slot], o.py[slot], z0, rx, ry);
+            } else {
+                q = p1;
+            }
+            add_piece(prev, q, lam, lat, L, klo, nb, out);
+            prev = q;
+        }
+    }
+}
+
+__global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
+                                  int32_t *__restrict__ band_hi) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < m.n_faces;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = 0;
+        int64_t s, e;
+        if (m.L >= 2 && cell_span(m, f, s, e) && e > s) {
+            double zmin = 2.0, zmax = -2.0, wind = 0.0;
+            bool ok = true, any = false;
+            double a[3], b[3];
+            ok = node_at(m, s, a);
+            for (int64_t i = s; i < e && ok; ++i) {
+                if (!(ok = node_at(m, i + 1 < e ? i + 1 : s, b))) break;
+                double zl, zh;
+                if (z_range_fp64(a, b, zl, zh)) {
+                    zmin = fmin(zmin, zl);
+                    zmax = fmax(zmax, zh);
+                    any = true;
+                }
+                // arcs from or to a pole step no longitude (atan2 of signed zeros)
+                if ((a[0] != 0.0 || a[1] != 0.0) && (b[0] != 0.0 || b[1] != 0.0))
+                    wind += atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1]);
+                a[0] = b[0];
+                a[1] = b[1];
+                a[2] = b[2];
+            }
+            if (ok && any) {
+                const double w = rint(wind / kTwoPi);
+                if (w >= 1.0) zmax = 1.0;
+                if (w <= -1.0) zmin = -1.0;
+                if (!(zmax < m.lat[0] || zmin > m.lat[m.L - 1])) {
+                    int64_t klo = upper_bound_ord(m.lat, m.L, ord64(zmin)) - 1;
+                    int64_t khi = upper_bound_ord(m.lat, m.L, ord64(zmax)) - 1;
+                    klo = klo < 0 ? 0 : klo;
+                    khi = khi > m.L - 2 ? m.L - 2 : khi;
+                    if (khi >= klo) {
+                        lo = (int32_t)klo;
+                        hi = (int32_t)(khi + 1);
+                    }
+                }
+            }
+        }
+        band_lo[f] = lo;
+        band_hi[f] = hi;
+    }
+}
+
+template <int Mode>
+__global__ void __launch_bounds__(kAreaThreads)
+    band_area_kernel(Mesh m, const int32_t *__restrict__ band_lo,
+                     const int32_t *__restrict__ band_hi, const long long *__restrict__ offsets,
+                     double *__restrict__ areas, int64_t cap) {
+    extern __shared__ double s_lat[];
+    const double *lat = m.lat;
+    if (m.L <= kSmemLat) {
+        for (int64_t i = threadIdx.x; i < m.L; i += blockDim.x) s_lat[i] = m.lat[i];
+        __syncthreads();
+        lat = s_lat;
+    }
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < m.n_faces;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t klo = band_lo[f];
+        const int64_t nb = (int64_t)band_hi[f] - klo;
+        if (nb <= 0) continue;
+        if (klo < 0 || klo + nb > m.L - 1) {
+            atomicOr(m.status, kStatusInvalid);
+            continue;
+        }
+        const long long off = offsets[f];
+        if (off < 0 || off + nb > cap) {
+            atomicOr(m.status, kStatusCapacity);
+            continue;
+        }
+        double *out = areas + off;
+        for (int64_t j = 0; j < nb; ++j) out[j] = 0.0;
+        int64_t s, e;
+        if (!cell_span(m, f, s, e) || e - s < 2) continue;
+        const int64_t nv = e - s;
+        // the first node off the poles: lambda = 0 there, and the cut to a
+        // pole inside the cell starts there
+        int64_t st = -1;
+        double a[3], ua[3];
+        for (int64_t i = 0; i < nv; ++i) {
+            if (!node_at(m, s + i, a)) break;
+            unit(a, ua);
+            if (!(sqrt(fma(ua[0], ua[0], ua[1] * ua[1])) < kPoleRho)) {
+                st = i;
+                break;
+            }
+        }
+        if (st < 0) continue;
+        const double z_st = ua[2];
+        double ax = ua[0], ay = ua[1];  // last node off the poles
+        double lam_anc = 0.0;           // its unwrapped longitude
+        bool ok = true;
+        for (int64_t t = 0; t < nv; ++t) {
+            int64_t ib = st + t + 1;
+            if (ib >= nv) ib -= nv;
+            double b[3], ub[3];
+            if (!(ok = node_at(m, s + ib, b))) break;
+            unit(b, ub);
+            const bool a_pole = sqrt(fma(ua[0], ua[0], ua[1] * ua[1])) < kPoleRho;
+            const bool b_pole = sqrt(fma(ub[0], ub[0], ub[1] * ub[1])) < kPoleRho;
+            // a pole has no longitude: an arc to or from it is a meridian, and
+            // lambda steps from the last node off the poles to the next one
+            const double lam_b = b_pole ? lam_anc : lam_anc + delta_lon(ax, ay, ub[0], ub[1]);
+            if (!(a_pole && b_pole)) {
+                if (!a_pole)
+                    arc_pieces<Mode>(a, b, ua, ub, ua[0], ua[1], lam_anc, lat, m.L, klo, nb, out);
+                else
+                    arc_pieces<Mode>(a, b, ua, ub, ub[0], ub[1], lam_b, lat, m.L, klo, nb, out);
+            }
+            if (!b_pole) {
+                ax = ub[0];
+                ay = ub[1];
+                lam_anc = lam_b;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a[c] = b[c];
+                ua[c] = ub[c];
+            }
+        }
+        if (!ok) continue;
+        const double w = rint(lam_anc / kTwoPi);
+        if (w != 0.0) {
+            for (int64_t j = 0; j < nb; ++j) {
+                const double zl = lat[klo + j], zh = lat[klo + j + 1];
+                const double lo = w > 0.0 ? fmax(zl, z_st) : fmax(zl, -1.0);
+                const double hi = w > 0.0 ? fmin(zh, 1.0) : fmin(zh, z_st);
+                if (hi > lo) out[j] += kTwoPi * (hi - lo);
+            }
+        }
+    }
+}
+
+// ---- zonal sums in 128-bit fixed point ---------------------------------------------
+// x * 2^80 rounded to an integer (halves away from zero) as a 128-bit two's
+// complement (hi, lo); false for a non-finite x or |x| >= 2^46
+__device__ __forceinline__ bool to_fixed(double x, unsigned long long &lo,
+                                         unsigned long long &hi) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    lo = hi = 0ull;
+    if (ex == 0) return true;  // zero or subnormal: far below 2^-80
+    if (ex == 0x7ff) return false;
+    const unsigned long long M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = ex - 1075 + kFracBits;  // x * 2^80 = M * 2^sh
+    if (sh > 73) return false;             // M * 2^sh >= 2^126
+    if (sh >= 64) {
+        hi = M << (sh - 64);
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = M >> (64 - sh);
+    } else if (sh == 0) {
+        lo = M;
+    } else if (-sh <= 54) {
+        const int r = -sh;
+        lo = (M + (1ull << (r - 1))) >> r;
+    }
+    if (bits >> 63) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    return true;
+}
+
+// (hi, lo) += (vhi, vlo) modulo 2^128 with two 64-bit atomics: each wrap of
+// the low word carries once into the high word, whatever the order
+__device__ __forceinline__ void add128(unsigned long long *acc, unsigned long long vlo,
+                                       unsigned long long vhi) {
+    if (vlo == 0ull && vhi == 0ull) return;
+    const unsigned long long old = atomicAdd(acc, vlo);
+    const unsigned long long up = vhi + (old + vlo < old ? 1ull : 0ull);
+    if (up) atomicAdd(acc + 1, up);
+}
+
+// the 128-bit fixed-point value as the nearest double
+__device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned long long hi) {
+    const bool neg = (hi >> 63) != 0ull;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    double v;
+    if (hi == 0ull) {
+        v = ldexp(__ull2double_rn(lo), -kFracBits);
+    } else {
+        const int c = __clzll((long long)hi);
+        unsigned long long top = c ? ((hi << c) | (lo >> (64 - c))) : hi;
+        const unsigned long long rest = lo << c;
+        top |= rest != 0ull ? 1ull : 0ull;  // sticky: below the rounding position
+        v = ldexp(__ull2double_rn(top), 64 - c - kFracBits);
+    }
+    return neg ? -v : v;
+}
+
+__global__ void __launch_bounds__(kZonalThreads)
+    zonal_sum_kernel(const int32_t *__restrict__ band_lo, const int32_t *__restrict__ band_hi,
+                     const long long *__restrict__ offsets, int64_t F,
+                     const double *__restrict__ areas, const double *__restrict__ field,
+                     int64_t n_bands, unsigned long long *__restrict__ acc, int use_smem,
+                     unsigned *status) {
+    extern __shared__ unsigned long long s_acc[];
+    unsigned long long *tgt = acc;
+    if (use_smem) {
+        for (int64_t i = threadIdx.x; i < 4 * n_bands; i += blockDim.x) s_acc[i] = 0ull;
+        __syncthreads();
+        tgt = s_acc;
+    }
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t klo = band_lo[f];
+        const int64_t nb = (int64_t)band_hi[f] - klo;
+        if (nb <= 0) continue;
+        const long long off = offsets[f];
+        const double fv = field[f];
+        for (int64_t j = 0; j < nb; ++j) {
+            const int64_t k = klo + j;
+            if (k < 0 || k >= n_bands || off < 0) {
+                atomicOr(status, kStatusInvalid);
+                break;
+            }
+            const double A = areas[off + j];
+            unsigned long long lo, hi;
+            if (to_fixed(fv * A, lo, hi))
+                add128(tgt + 4 * k, lo, hi);
+            else
+                atomicOr(status, kStatusInvalid);
+            if (to_fixed(A, lo, hi))
+                add128(tgt + 4 * k + 2, lo, hi);
+            else
+                atomicOr(status, kStatusInvalid);
+        }
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < 2 * n_bands; i += blockDim.x)
+            add128(acc + 2 * i, s_acc[2 * i], s_acc[2 * i + 1]);
+    }
+}
+
+__global__ void zonal_finish_kernel(const unsigned long long *__restrict__ acc, int64_t n_bands,
+                                    double *__restrict__ out_fa, double *__restrict__ out_a) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_bands;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        out_fa[k] = from_fixed(acc[4 * k], acc[4 * k + 1]);
+        out_a[k] = from_fixed(acc[4 * k + 2], acc[4 * k + 3]);
+    }
+}
+
+// ---- launchers -------------------------------------------------------------------
+template <int Mode>
+static cudaError_t launch_areas_mode(const Mesh &m, const int32_t *lo, const int32_t *hi,
+                                     const long long *off, double *areas, int64_t cap,
+                                     int sm_count, cudaStream_t s) {
+    const size_t smem = m.L <= kSmemLat ? (size_t)m.L * sizeof(double) : 0;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, band_area_kernel<Mode>, kAreaThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (m.n_faces + kAreaThreads - 1) / kAreaThreads;
+    const int64_t grid = std::min<int64_t>(need, (int64_t)per_sm * sm_count);
+    band_area_kernel<Mode><<<(unsigned)grid, kAreaThreads, smem, s>>>(m, lo, hi, off, areas, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace sphx
+
+using namespace sphx;
+
+namespace {
+
+bool valid_mesh(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+                const int64_t *face_offsets, const int32_t *face_nodes, int64_t n_face_nodes,
+                int64_t n_faces, const double *lat_z, int64_t n_lat) {
+    return ctx && n_faces >= 0 && n_nodes >= 0 && n_face_nodes >= 0 && n_lat >= 2 &&
+           n_lat <= INT32_MAX && (n_faces == 0 || (nodes && face_offsets && face_nodes)) &&
+           lat_z;
+}
+
+Mesh make_mesh(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+               const int64_t *face_offsets, const int32_t *face_nodes, int64_t n_face_nodes,
+               int64_t n_faces, const double *lat_z, int64_t n_lat) {
+    Mesh m;
+    m.nodes = nodes;
+    m.n_nodes = n_nodes;
+    m.face_offsets = face_offsets;
+    m.face_nodes = face_nodes;
+    m.n_face_nodes = n_face_nodes;
+    m.n_faces = n_faces;
+    m.lat = lat_z;
+    m.L = n_lat;
+    m.status = ctx->status;
+    return m;
+}
+
+}  // namespace
+
+extern "C" sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+                                        const int64_t *face_offsets, const int32_t *face_nodes,
+                                        int64_t n_face_nodes, int64_t n_faces,
+                                        const double *lat_z, int64_t n_lat, int32_t *band_lo,
+                                        int32_t *band_hi, int64_t *area_offsets,
+                                        sphx_stream stream) {
+    if (!valid_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z,
+                    n_lat) ||
+        !area_offsets || (n_faces > 0 && (!band_lo || !band_hi)))
+        return SPHX_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPHX_CUDA(cudaSetDevice(ctx->device));
+    if (n_faces == 0) {
+        SPHX_CUDA(cudaMemsetAsync(area_offsets, 0, sizeof(int64_t), s));
+        return SPHX_OK;
+    }
+    sphx_status st = ensure_band_scratch(ctx, n_faces);
+    if (st != SPHX_OK) return st;
+    const Mesh m =
+        make_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z, n_lat);
+    const int64_t grid = std::min<int64_t>((n_faces + 255) / 256, (int64_t)ctx->sm_count * 8);
+    band_range_kernel<<<(unsigned)grid, 256, 0, s>>>(m, band_lo, band_hi);
+    SPHX_CUDA(cudaGetLastError());
+    SPHX_CUDA(launch_scan(band_lo, band_hi, n_faces, ctx->band_block_sums,
+                          reinterpret_cast<long long *>(area_offsets), s));
+    return SPHX_OK;
+}
+
+extern "C" sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, int64_t n_nodes,
+                                       const int64_t *face_offsets, const int32_t *face_nodes,
+                                       int64_t n_face_nodes, int64_t n_faces,
+                                       const double *lat_z, int64_t n_lat,
+                                       const int32_t *band_lo, const int32_t *band_hi,
+                                       const int64_t *area_offsets, sphx_mode mode,
+                                       double *areas, int64_t areas_cap, sphx_stream stream) {
+    if (!valid_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z,
+                    n_lat) ||
+        areas_cap < 0 || (n_faces > 0 && (!band_lo || !band_hi || !area_offsets)) ||
+        (areas_cap > 0 && !areas))
+        return SPHX_ERR_INVALID_ARG;
+    if (n_faces == 0) return SPHX_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPHX_CUDA(cudaSetDevice(ctx->device));
+    const Mesh m =
+        make_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z, n_lat);
+    const long long *off = reinterpret_cast<const long long *>(area_offsets);
+    cudaError_t e;
+    switch (mode) {
+        case SPHX_MODE_DIRECT_FP64:
+            e = launch_areas_mode<kDirect>(m, band_lo, band_hi, off, areas, areas_cap,
+                                           ctx->sm_count, s);
+            break;
+        case SPHX_MODE_EFT_FP64:
+            e = launch_areas_mode<kEftFp64>(m, band_lo, band_hi, off, areas, areas_cap,
+                                            ctx->sm_count, s);
+            break;
+        case SPHX_MODE_EFT_FF32:
+            e = launch_areas_mode<kEftFf32>(m, band_lo, band_hi, off, areas, areas_cap,
+                                            ctx->sm_count, s);
+            break;
+        case SPHX_MODE_EFT_FP64_PRINTED:
+            e = launch_areas_mode<kEftFp64Printed>(m, band_lo, band_hi, off, areas, areas_cap,
+                                                   ctx->sm_count, s);
+            break;
+        case SPHX_MODE_WIDE_INT:
+            e = launch_areas_mode<kWideInt>(m, band_lo, band_hi, off, areas, areas_cap,
+                                            ctx->sm_count, s);
+            break;
+        default:
+            return SPHX_ERR_INVALID_ARG;
+    }
+    SPHX_CUDA(e);
+    return SPHX_OK;
+}
+
+extern "C" sphx_status sphx_zonal_sums(sphx_context *ctx, const int32_t *band_lo,
+                                       const int32_t *band_hi, const int64_t *area_offsets,
+                                       int64_t n_faces, const double *areas, const double *field,
+                                       int64_t n_lat, double *out_fa, double *out_a,
+                                       sphx_stream stream) {
+    if (!ctx || n_faces < 0 || n_lat < 2 || !out_fa || !out_a ||
+        (n_faces > 0 && (!band_lo || !band_hi || !area_offsets || !areas || !field)))
+        return SPHX_ERR_INVALID_ARG;
+    const int64_t n_bands = n_lat - 1;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPHX_CUDA(cudaSetDevice(ctx->device));
+    sphx_status st = ensure_zonal_scratch(ctx, n_bands);
+    if (st != SPHX_OK) return st;
+    unsigned long long *acc = ctx->zonal_acc;
+    SPHX_CUDA(cudaMemsetAsync(acc, 0, 4 * n_bands * sizeof(unsigned long long), s));
+    if (n_faces > 0) {
+        const int use_smem = n_bands <= kSmemBands ? 1 : 0;
+        const size_t smem = use_smem ? (size_t)(4 * n_bands) * sizeof(unsigned long long) : 0;
+        if (smem > 48 * 1024)
+            SPHX_CUDA(cudaFuncSetAttribute(zonal_sum_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t grid =
+            std::min<int64_t>((n_faces + kZonalThreads - 1) / kZonalThreads, (int64_t)ctx->sm_count * 2);
+        zonal_sum_kernel<<<(unsigned)grid, kZonalThreads, smem, s>>>(
+            band_lo, band_hi, reinterpret_cast<const long long *>(area_offsets), n_faces, areas,
+            field, n_bands, acc, use_smem, ctx->status);
+        SPHX_CUDA(cudaGetLastError());
+    }
+    const int64_t g2 = std::min<int64_t>((n_bands + 255) / 256, 1024);
+    zonal_finish_kernel<<<(unsigned)g2, 256, 0, s>>>(acc, n_bands, out_fa, out_a);
+    SPHX_CUDA(cudaGetLastError());
+    return SPHX_OK;
+}

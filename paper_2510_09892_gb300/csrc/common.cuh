@@ -15,7 +15,7 @@
 namespace sphx {
 
 // device status word bits (OR-ed by kernels, read by sphx_sync_status)
-enum : unsigned { kStatusCapacity = 1u, kStatusTimeout = 2u, kStatusScratch = 4u };
+enum : unsigned { kStatusCapacity = 1u, kStatusTimeout = 2u, kStatusScratch = 4u, kStatusInvalid = 8u };
 
 // bound on the ordered compaction's look-back spin: each iteration is one L2
 // read plus a 64 ns sleep (~0.5 us), so the wait gives up after about a second
@@ -114,5 +114,15 @@ struct sphx_context {
     sphx::RaggedShape shape;
     std::map<sphx::GraphKey, cudaGraphExec_t> graphs;
     sphx::HostStaging host;
+    long long *band_block_sums = nullptr;  // band ranges' prefix sum: per scan block
+    int64_t band_faces = 0;                // cells the buffer serves
+    unsigned long long *zonal_acc = nullptr;  // zonal sums: 4 words per band
+    int64_t zonal_bands = 0;
     std::mutex mu;
 };
+
+namespace sphx {
+// runtime.cu: per-context scratch of the band-area calls (grown on demand)
+sphx_status ensure_band_scratch(sphx_context *ctx, int64_t faces);
+sphx_status ensure_zonal_scratch(sphx_context *ctx, int64_t bands);
+}  // namespace sphx

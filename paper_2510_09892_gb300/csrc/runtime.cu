@@ -87,6 +87,42 @@ void drop_graphs(sphx_context *ctx) {
     ctx->graphs.clear();
 }
 
+}  // namespace
+
+sphx_status sphx::ensure_band_scratch(sphx_context *ctx, int64_t faces) {
+    if (ctx->band_block_sums && ctx->band_faces >= faces) return SPHX_OK;
+    SPHX_CUDA(cudaDeviceSynchronize());  // nothing may still use the old buffer
+    cudaFree(ctx->band_block_sums);
+    ctx->band_block_sums = nullptr;
+    ctx->band_faces = 0;
+    const int64_t cap = faces + faces / 4 + 1024;
+    if (cudaMalloc(&ctx->band_block_sums, (scan_blocks_for(cap) + 1) * sizeof(long long)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        ctx->band_block_sums = nullptr;
+        return SPHX_ERR_NOMEM;
+    }
+    ctx->band_faces = cap;
+    return SPHX_OK;
+}
+
+sphx_status sphx::ensure_zonal_scratch(sphx_context *ctx, int64_t bands) {
+    if (ctx->zonal_acc && ctx->zonal_bands >= bands) return SPHX_OK;
+    SPHX_CUDA(cudaDeviceSynchronize());
+    cudaFree(ctx->zonal_acc);
+    ctx->zonal_acc = nullptr;
+    ctx->zonal_bands = 0;
+    if (cudaMalloc(&ctx->zonal_acc, 4 * bands * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->zonal_acc = nullptr;
+        return SPHX_ERR_NOMEM;
+    }
+    ctx->zonal_bands = bands;
+    return SPHX_OK;
+}
+
+namespace {
+
 sphx_status ensure_scratch(sphx_context *ctx, int64_t E) {
     RaggedScratch &s = ctx->scratch;
     if (s.E >= E && s.ring) return SPHX_OK;
@@ -362,6 +398,8 @@ void sphx_destroy(sphx_context *ctx) {
     drop_graphs(ctx);
     free_scratch(ctx->scratch);
     free_host_staging(ctx->host);
+    cudaFree(ctx->band_block_sums);
+    cudaFree(ctx->zonal_acc);
     cudaFree(ctx->status);
     cudaStreamDestroy(ctx->capture_stream);
     delete ctx;
@@ -440,7 +478,7 @@ sphx_status sphx_sync_status(sphx_context *ctx, sphx_stream stream) {
     SPHX_CUDA(cudaMemcpy(&h, ctx->status, sizeof h, cudaMemcpyDeviceToHost));
     SPHX_CUDA(cudaMemset(ctx->status, 0, sizeof h));
     if (h & kStatusTimeout) return SPHX_ERR_TIMEOUT;
-    if (h & kStatusScratch) return SPHX_ERR_INVALID_ARG;
+    if (h & (kStatusScratch | kStatusInvalid)) return SPHX_ERR_INVALID_ARG;
     if (h & kStatusCapacity) return SPHX_ERR_CAPACITY;
     return SPHX_OK;
 }

@@ -65,6 +65,11 @@ _SIGS = {
                                              ctypes.c_int, _vp, _i64, _vp, _vp]),
     "sphx_intersect_ragged_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64,
                                                      ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "sphx_band_ranges": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp,
+                                        _vp, _vp]),
+    "sphx_band_areas": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp,
+                                       _vp, ctypes.c_int, _vp, _i64, _vp]),
+    "sphx_zonal_sums": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "sphx_sync_status": (ctypes.c_int, [_vp, _vp]),
     "sphx_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     "sphx_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
@@ -336,6 +341,73 @@ def sphx_autotune_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, o
                                     _ptr(out_total), _stream(stream), ctypes.byref(ms))
     _check(st, "sphx_autotune_ragged")
     return ms.value
+
+
+# ------------------------------------------------------------- band areas --
+def _mesh_args(nodes, face_offsets, face_nodes, lat_z):
+    _dev_tensor(nodes, torch.float64, "nodes")
+    if nodes.dim() != 2 or nodes.shape[1] != 3:
+        raise ValueError("nodes must have shape (n_nodes, 3)")
+    _dev_tensor(face_offsets, torch.int64, "face_offsets")
+    _dev_tensor(face_nodes, torch.int32, "face_nodes")
+    _dev_tensor(lat_z, torch.float64, "lat_z")
+    return (_ptr(nodes), int(nodes.shape[0]), _ptr(face_offsets), _ptr(face_nodes),
+            int(face_nodes.numel()), int(face_offsets.numel()) - 1, _ptr(lat_z), int(lat_z.numel()))
+
+
+def sphx_band_ranges(ctx: Context, nodes, face_offsets, face_nodes, lat_z, band_lo, band_hi,
+                     area_offsets, stream=None):
+    """Bands [band_lo, band_hi) per cell and the output offsets (see include/sphx.h).
+
+    nodes: (n_nodes, 3) float64; face_offsets: (n_faces + 1,) int64; face_nodes:
+    int32; lat_z: ascending float64; band_lo, band_hi: (n_faces,) int32;
+    area_offsets: (n_faces + 1,) int64 (all CUDA tensors).
+    """
+    args = _mesh_args(nodes, face_offsets, face_nodes, lat_z)
+    F = args[5]
+    _dev_tensor(band_lo, torch.int32, "band_lo", (F,))
+    _dev_tensor(band_hi, torch.int32, "band_hi", (F,))
+    _dev_tensor(area_offsets, torch.int64, "area_offsets", (F + 1,))
+    _check(lib().sphx_band_ranges(ctx.handle, *args, _ptr(band_lo), _ptr(band_hi),
+                                  _ptr(area_offsets), _stream(stream)), "sphx_band_ranges")
+
+
+def sphx_band_areas(ctx: Context, nodes, face_offsets, face_nodes, lat_z, band_lo, band_hi,
+                    area_offsets, areas, mode="wide", stream=None):
+    """Area of each cell in each band of its range, into areas (float64 CUDA tensor)."""
+    args = _mesh_args(nodes, face_offsets, face_nodes, lat_z)
+    _dev_tensor(areas, torch.float64, "areas")
+    _check(lib().sphx_band_areas(ctx.handle, *args, _ptr(band_lo), _ptr(band_hi),
+                                 _ptr(area_offsets), _mode(mode), _ptr(areas), int(areas.numel()),
+                                 _stream(stream)), "sphx_band_areas")
+
+
+def sphx_zonal_sums(ctx: Context, band_lo, band_hi, area_offsets, areas, field, n_lat, out_fa,
+                    out_a, stream=None):
+    """Per band: sum of field * area (out_fa) and of area (out_a), order-independent."""
+    F = int(band_lo.numel())
+    _dev_tensor(field, torch.float64, "field", (F,))
+    _dev_tensor(out_fa, torch.float64, "out_fa", (int(n_lat) - 1,))
+    _dev_tensor(out_a, torch.float64, "out_a", (int(n_lat) - 1,))
+    _check(lib().sphx_zonal_sums(ctx.handle, _ptr(band_lo), _ptr(band_hi), _ptr(area_offsets), F,
+                                 _ptr(areas), _ptr(field), int(n_lat), _ptr(out_fa), _ptr(out_a),
+                                 _stream(stream)), "sphx_zonal_sums")
+
+
+def band_areas(ctx: Context, nodes, face_offsets, face_nodes, lat_z, mode="wide", stream=None):
+    """Both band-area calls with freshly allocated outputs (reads the entry count
+    back to the host once). Returns (band_lo, band_hi, area_offsets, areas)."""
+    F = int(face_offsets.numel()) - 1
+    dev = nodes.device
+    band_lo = torch.empty(F, dtype=torch.int32, device=dev)
+    band_hi = torch.empty(F, dtype=torch.int32, device=dev)
+    off = torch.empty(F + 1, dtype=torch.int64, device=dev)
+    sphx_band_ranges(ctx, nodes, face_offsets, face_nodes, lat_z, band_lo, band_hi, off, stream)
+    total = int(off[-1].item())
+    areas = torch.empty(max(total, 1), dtype=torch.float64, device=dev)
+    sphx_band_areas(ctx, nodes, face_offsets, face_nodes, lat_z, band_lo, band_hi, off, areas,
+                    mode, stream)
+    return band_lo, band_hi, off, areas[:total]
 
 
 def hits_to_numpy(out, total: int):

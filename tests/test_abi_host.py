@@ -67,6 +67,29 @@ def test_ragged_argument_errors_before_launch():
     assert g(FAKE, FAKE, FAKE, 1, 10, FAKE, FAKE, 5, None, FAKE, None) == sphx.ERR_INVALID_ARG
 
 
+def test_band_area_argument_errors_before_launch():
+    L = sphx.lib()
+    ctx = ctypes.c_void_p(FAKE)
+    r = L.sphx_band_ranges
+    # no context, too few latitudes, negative sizes, missing outputs
+    assert r(None, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 1, FAKE, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert r(ctx, FAKE, 10, FAKE, FAKE, 40, -1, FAKE, 5, FAKE, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, None, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, None, None) == sphx.ERR_INVALID_ARG
+    a = L.sphx_band_areas
+    assert a(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, FAKE, 4, FAKE, -1,
+             None) == sphx.ERR_INVALID_ARG
+    assert a(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, None, 4, FAKE, 10,
+             None) == sphx.ERR_INVALID_ARG
+    assert a(ctx, None, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, FAKE, 4, FAKE, 10,
+             None) == sphx.ERR_INVALID_ARG
+    z = L.sphx_zonal_sums
+    assert z(None, FAKE, FAKE, FAKE, 10, FAKE, FAKE, 5, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert z(ctx, FAKE, FAKE, FAKE, 10, FAKE, FAKE, 1, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+    assert z(ctx, FAKE, FAKE, FAKE, 10, FAKE, None, 5, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
+
+
 def test_tuning_validation_without_device():
     L = sphx.lib()
     assert L.sphx_set_tuning(None, None) == sphx.ERR_INVALID_ARG
