@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -215,11 +216,20 @@ def main():
                     help="skip the ragged (regridding) leg reported beside the headline")
     ap.add_argument("--mode", default="wide", choices=["wide", "eft", "direct", "ff32"],
                     help="headline evaluation mode (the others are timed beside it)")
+    ap.add_argument("--zonal-only", action="store_true",
+                    help="run only the zonal-mean leg and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.zonal_only:
+        import torch
+        from paper_2510_09892_gb300 import sphx
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"zonal_mean": zonal_leg(sphx, torch, dev, args, args.mode)}), flush=True)
+        return
 
     rank, world, local = dist_env()
     # the process pools start before CUDA does ('spawn' regardless)
@@ -302,6 +312,7 @@ def main():
 
     arcs = arcs_leg(sphx, torch, dev, args, flush) if rank == 0 else None
     ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
+    zonal = zonal_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
     meshes = (meshes_leg(sphx, torch, dev, args, head, mesh_pool)
               if rank == 0 and not args.no_ragged else None)
 
@@ -364,6 +375,8 @@ def main():
         line["arc_x_arc"] = arcs
     if ragged is not None:
         line["ragged_regridding"] = ragged
+    if zonal is not None:
+        line["zonal_mean"] = zonal
     if meshes is not None:
         line["ragged_meshes"] = meshes
     print(json.dumps(line), flush=True)
@@ -449,6 +462,66 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
                 "ms_per_step": ms, "edges_per_s": E / (ms * 1e-3),
                 "pairs_per_s": pairs / (ms * 1e-3), "hits_per_s": hits / (ms * 1e-3),
                 "hbm_frac": (48 * E + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak()}
+    return res
+
+
+def zonal_leg(sphx, torch, dev, args, head) -> dict:
+    """The zonal-mean step (not the headline) on the regridding workload: the
+    cubed sphere with 1024 x 1024 cells per face (6,291,456 node-indexed
+    quadrilaterals) against the 721 latitudes of a 0.25-degree grid. One step
+    is sphx_band_ranges (bands per cell, prefix sum), sphx_band_areas (area of
+    every cell in every band it meets) and sphx_zonal_sums (per-band sums of
+    field * area and area). The mesh (300 MB) exceeds L2, so no flush."""
+    nodes, off, fn = W.cubed_sphere_cells(1024)
+    lat = W.latlon_latitudes(721)
+    F, nb = len(off) - 1, len(lat) - 1
+    dn, do, df, dl = (torch.from_numpy(x).to(dev) for x in (nodes, off, fn, lat))
+    field = torch.from_numpy(nodes[fn[0::4], 2].copy()).to(dev)  # z of each cell's first node
+    lo = torch.empty(F, dtype=torch.int32, device=dev)
+    hi = torch.empty(F, dtype=torch.int32, device=dev)
+    ao = torch.empty(F + 1, dtype=torch.int64, device=dev)
+    fa = torch.empty(nb, dtype=torch.float64, device=dev)
+    aa = torch.empty(nb, dtype=torch.float64, device=dev)
+    cur = torch.cuda.current_stream(dev)
+    res = {"workload": "cubed sphere N=1024 (6,291,456 cells) x 721 latitudes (0.25 deg): "
+                       "band ranges + band areas + zonal sums", "cells": F, "modes": {}}
+    exact_bands = 2 * math.pi * np.diff(lat)
+    with sphx.Context(dev.index or 0) as ctx:
+        sphx.sphx_band_ranges(ctx, dn, do, df, dl, lo, hi, ao, stream=cur)
+        entries = int(ao[-1].item())
+        areas = torch.empty(entries, dtype=torch.float64, device=dev)
+        res["band_entries"] = entries
+
+        def step(mode, ev=None):
+            sphx.sphx_band_ranges(ctx, dn, do, df, dl, lo, hi, ao, stream=cur)
+            if ev is not None:
+                ev[0].record(cur)
+            sphx.sphx_band_areas(ctx, dn, do, df, dl, lo, hi, ao, areas, mode, stream=cur)
+            if ev is not None:
+                ev[1].record(cur)
+            sphx.sphx_zonal_sums(ctx, lo, hi, ao, areas, field, len(lat), fa, aa, stream=cur)
+
+        for mode in (head, "eft", "direct"):
+            for _ in range(args.warmup):
+                step(mode)
+            if ctx.sync_status(cur) != sphx.OK:
+                raise RuntimeError("band-area call reported an error")
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            e0.record(cur)
+            for i in range(args.steps):
+                step(mode, kev[i])
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            k_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+            cons = float(np.abs(aa.cpu().numpy() - exact_bands).max())
+            res["modes"][mode] = {
+                "ms_per_step": ms, "cells_per_s": F / (ms * 1e-3),
+                "band_areas_per_s": entries / (ms * 1e-3), "area_kernel_ms": k_ms,
+                "max_abs_band_total_error": cons}
     return res
 
 

@@ -50,7 +50,7 @@ namespace sphx {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int kAreaThreads = 128;
-constexpr int64_t kSmemLat = 4096;  // latitudes staged in shared memory up to this count
+constexpr int64_t kSmemLat = 2048;  // latitudes (and their radii) staged in shared memory up to this count
 constexpr int kFracBits = 80;       // zonal sums: fixed point with 2^-80 resolution
 constexpr int kZonalThreads = 256;
 constexpr int64_t kSmemBands = 3072;  // bands accumulated in shared memory up to this count
@@ -96,7 +96,7 @@ __device__ __forceinline__ bool node_at(const Mesh &m, int64_t i, double (&v)[3]
 }
 
 __device__ __forceinline__ void unit(const double (&v)[3], double (&u)[3]) {
-    const double r = 1.0 / sqrt(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
+    const double r = rsqrt(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
     u[0] = v[0] * r;
     u[1] = v[1] * r;
     u[2] = v[2] * r;
@@ -105,92 +105,126 @@ __device__ __forceinline__ void unit(const double (&v)[3], double (&u)[3]) {
 // a point of an arc with what the boundary integral needs
 struct Pt {
     double x, y, z;  // unit vector
-    double rho;      // sqrt(x^2 + y^2)
-    double t;        // tan(latitude / 2) = z / (1 + rho)
-    double d;        // longitude from the arc's reference meridian, in [-pi, pi]
-};                   // (rho = 0 and no longitude at a pole)
+    double rho;      // sqrt(x^2 + y^2); 0 at a pole
+};
 
-// angle from the meridian of unit vector r to that of unit vector p (xy
-// parts): the cross product from the differences p - r, r x p = r x (p - r),
-// so that a small angle comes out accurate relative to itself (the plain
-// products would leave an absolute error of a unit of rounding)
-__device__ __forceinline__ double delta_lon(double rx, double ry, double x, double y) {
-    return atan2(rx * (y - ry) - ry * (x - rx), fma(rx, x, ry * y));
-}
-
-__device__ __forceinline__ Pt make_pt(double x, double y, double z, double rx, double ry) {
+__device__ __forceinline__ Pt make_pt(double x, double y, double z) {
     Pt p;
     p.x = x;
     p.y = y;
     p.z = z;
-    p.rho = sqrt(fma(x, x, y * y));
-    if (p.rho < kPoleRho) {
-        p.x = p.y = p.rho = p.d = 0.0;
-        p.t = z;
-        return p;
-    }
-    p.t = z / (1.0 + p.rho);
-    p.d = delta_lon(rx, ry, x, y);
+    const double r2 = fma(x, x, y * y);
+    if (r2 < kPoleRho * kPoleRho)
+        p.x = p.y = p.rho = 0.0;
+    else
+        p.rho = sqrt(r2);
     return p;
 }
 
-// piece p -> q of an arc whose longitudes are lam + d: add
-// lambda_q z_q - lambda_p z_p - T(p, q) to the band holding the piece's
-// midpoint. A piece from or to a pole runs along a meridian: lambda is the
-// other end's all along it and T = 0.
-__device__ __forceinline__ void add_piece(const Pt &p, const Pt &q, double lam, const double *lat,
-                                          int64_t L, int64_t klo, int64_t nb, double *out) {
-    const bool p_pole = p.rho == 0.0, q_pole = q.rho == 0.0;
-    if (p_pole && q_pole) return;
-    const double sx = p.x + q.x, sy = p.y + q.y, sz = p.z + q.z;
-    const double zm = sz / sqrt(fma(sx, sx, fma(sy, sy, sz * sz)));
-    const int64_t k = upper_bound_ord(lat, L, ord64(zm)) - 1;
-    if (k < klo || k >= klo + nb) return;
-    double T = 0.0;
-    if (!(p_pole || q_pole)) {
-        const double cr = p.x * (q.y - p.y) - p.y * (q.x - p.x);  // as in delta_lon
-        const double dt = fma(p.rho, q.rho, fma(p.x, q.x, p.y * q.y));
-        T = 2.0 * atan2(cr * (p.t + q.t), dt * fma(p.t, q.t, 1.0));
+// a crossing of the latitude z0, whose distance from the axis is
+// rho0 = sqrt((1 - z0)(1 + z0)) (per latitude, not per point)
+__device__ __forceinline__ Pt make_pt_at(double x, double y, double z0, double rho0) {
+    Pt p;
+    p.z = z0;
+    if (rho0 < kPoleRho) {
+        p.x = p.y = p.rho = 0.0;
+    } else {
+        p.x = x;
+        p.y = y;
+        p.rho = rho0;
     }
-    const double pd = p_pole ? q.d : p.d, qd = q_pole ? p.d : q.d;
-    const double I = fma(lam, q.z - p.z, fma(qd, q.z, -pd * p.z)) - T;
-    out[k - klo] += I;
+    return p;
 }
 
-// all pieces of the arc a -> b (raw a, b for Eq. 2.2; ua, ub of unit length),
-// longitudes lam + (angle from (rx, ry))
+__device__ __forceinline__ double rho_of_lat(double z) { return sqrt((1.0 - z) * (1.0 + z)); }
+
+// angle from the meridian of r to that of p (xy parts of unit vectors), with
+// the cross product taken from the differences, r x p = r x (p - r), so that a
+// small angle is accurate relative to itself
+__device__ __forceinline__ double delta_lon(double rx, double ry, double x, double y) {
+    return atan2(rx * (y - ry) - ry * (x - rx), fma(rx, x, ry * y));
+}
+
+// arctan x by its series x - x^3/3 + x^5/5 - x^7/7, for |x| <= 2^-9
+// (the next term is below 2^-84 |x|)
+__device__ __forceinline__ double atan_small(double x) {
+    const double x2 = x * x;
+    return fma(x * x2, fma(x2, fma(x2, -1.0 / 7.0, 1.0 / 5.0), -1.0 / 3.0), x);
+}
+
+// Piece p -> q of an arc; the longitude at p is lam + dp. With dl the
+// piece's longitude step, h = tan(dl / 2) from the xy cross and dot
+// products, and K = (t_p + t_q) / (1 + t_p t_q) for t = tan(latitude / 2)
+// = z / (1 + rho), the signed area between the piece and the equator is
+// T = 2 atan(K h), and the boundary integral of lambda dz over the piece is
+//   (lam + dp) (z_q - z_p) + dl z_q - T,
+// added to the band that holds the piece's midpoint. A piece from or to a
+// pole runs along a meridian: dl = T = 0. Returns the longitude offset at q.
+__device__ __forceinline__ double add_piece(const Pt &p, const Pt &q, double lam, double dp,
+                                            const double *lat, int64_t L, int64_t klo,
+                                            int64_t nb, double *out) {
+    if (p.rho == 0.0 && q.rho == 0.0) return dp;
+    double dl = 0.0, W = 0.0;  // W = dl z_q - T
+    if (p.rho != 0.0 && q.rho != 0.0) {
+        const double cr = p.x * (q.y - p.y) - p.y * (q.x - p.x);  // as in delta_lon
+        const double den = fma(p.rho, q.rho, fma(p.x, q.x, p.y * q.y));
+        const double h = cr / den;
+        const double op = 1.0 + p.rho, oq = 1.0 + q.rho;
+        const double K = fma(p.z, oq, q.z * op) / fma(op, oq, p.z * q.z);
+        if (fabs(h) <= 0.001953125) {
+            const double a = atan_small(h);
+            dl = 2.0 * a;
+            W = 2.0 * fma(q.z, a, -atan_small(K * h));
+        } else {
+            dl = 2.0 * atan(h);
+            W = fma(dl, q.z, -2.0 * atan(K * h));
+        }
+    }
+    const double sx = p.x + q.x, sy = p.y + q.y, sz = p.z + q.z;
+    const double zm = sz * rsqrt(fma(sx, sx, fma(sy, sy, sz * sz)));
+    const int64_t k = upper_bound_ord(lat, L, ord64(zm)) - 1;
+    if (k >= klo && k < klo + nb) out[k - klo] += fma(lam + dp, q.z - p.z, W);
+    return dp + dl;
+}
+
+// All pieces of the arc a -> b (raw a, b for Eq. 2.2; ua, ub of unit length,
+// pa, pb their points) whose longitudes are lam + (offset from a's meridian,
+// 0 at a). rho_lat: the latitudes' radii, or null. Returns the offset at b
+// (the arc's longitude step).
 template <int Mode>
-__device__ __forceinline__ void arc_pieces(const double (&a)[3], const double (&b)[3],
-                                           const double (&ua)[3], const double (&ub)[3],
-                                           double rx, double ry, double lam, const double *lat,
-                                           int64_t L, int64_t klo, int64_t nb, double *out) {
+__device__ __forceinline__ double arc_pieces(const double (&a)[3], const double (&b)[3],
+                                             const double (&ua)[3], const double (&ub)[3],
+                                             const Pt &pa, const Pt &pb, double lam,
+                                             const double *lat, const double *rho_lat, int64_t L,
+                                             int64_t klo, int64_t nb, double *out) {
     const double nx = ua[1] * ub[2] - ua[2] * ub[1];
     const double ny = ua[2] * ub[0] - ua[0] * ub[2];
     const double nz = ua[0] * ub[1] - ua[1] * ub[0];
-    if (nx == 0.0 && ny == 0.0 && nz == 0.0) return;
+    if (nx == 0.0 && ny == 0.0 && nz == 0.0) return 0.0;
     // (n x x)_z, the vertical direction of travel at x: > 0 where the arc rises
     const double ga = nx * ua[1] - ny * ua[0];
     const double gb = nx * ub[1] - ny * ub[0];
     Pt ends[3];
     bool ups[2];
     int nruns;
-    ends[0] = make_pt(ua[0], ua[1], ua[2], rx, ry);
+    ends[0] = pa;
     if ((ga > 0.0 && gb < 0.0) || (ga < 0.0 && gb > 0.0)) {
         // the arc passes the great circle's highest point (rises, then falls)
         // or its lowest; the highest is (-nx nz, -ny nz, nx^2 + ny^2) / (|n| |n_xy|)
         const double S2 = fma(nx, nx, ny * ny);
         const double sc = (ga > 0.0 ? 1.0 : -1.0) / (sqrt(fma(nz, nz, S2)) * sqrt(S2));
-        ends[1] = make_pt(-nx * nz * sc, -ny * nz * sc, S2 * sc, rx, ry);
-        ends[2] = make_pt(ub[0], ub[1], ub[2], rx, ry);
+        ends[1] = make_pt(-nx * nz * sc, -ny * nz * sc, S2 * sc);
+        ends[2] = pb;
         ups[0] = ga > 0.0;
         ups[1] = !ups[0];
         nruns = 2;
     } else {
-        ends[1] = make_pt(ub[0], ub[1], ub[2], rx, ry);
+        ends[1] = pb;
         ups[0] = ub[2] >= ua[2];
         ups[1] = false;
         nruns = 1;
     }
+    double d = 0.0;
     for (int r = 0; r < nruns; ++r) {
         const bool up = ups[r];
         const Pt p1 = ends[r + 1];
@@ -208,14 +242,15 @@ __device__ __forceinline__ void arc_pieces(const double (&a)[3], const double (&
                 PairOut o;
                 intersect_pair<Mode>(a, b, z0, o);
                 if (!(o.count > 0 && o.hit[slot])) continue;
-                q = make_pt(o.px[slot], o.py[slot], z0, rx, ry);
+                q = make_pt_at(o.px[slot], o.py[slot], z0, rho_lat ? rho_lat[j] : rho_of_lat(z0));
             } else {
                 q = p1;
             }
-            add_piece(prev, q, lam, lat, L, klo, nb, out);
+            d = add_piece(prev, q, lam, d, lat, L, klo, nb, out);
             prev = q;
         }
     }
+    return d;
 }
 
 __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
@@ -232,14 +267,16 @@ __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
             for (int64_t i = s; i < e && ok; ++i) {
                 if (!(ok = node_at(m, i + 1 < e ? i + 1 : s, b))) break;
                 double zl, zh;
-                if (z_range_fp64(a, b, zl, zh)) {
+                if (z_range_fp32(a, b, zl, zh) || z_range_fp64(a, b, zl, zh)) {
                     zmin = fmin(zmin, zl);
                     zmax = fmax(zmax, zh);
                     any = true;
                 }
-                // arcs from or to a pole step no longitude (atan2 of signed zeros)
-                if ((a[0] != 0.0 || a[1] != 0.0) && (b[0] != 0.0 || b[1] != 0.0))
-                    wind += atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1]);
+                // the winding number needs each step only to well within pi:
+                // FP32; arcs from or to a pole step no longitude
+                const float ax = (float)a[0], ay = (float)a[1], bx = (float)b[0], by = (float)b[1];
+                if ((ax != 0.0f || ay != 0.0f) && (bx != 0.0f || by != 0.0f))
+                    wind += (double)atan2f(ax * by - ay * bx, ax * bx + ay * by);
                 a[0] = b[0];
                 a[1] = b[1];
                 a[2] = b[2];
@@ -266,16 +303,21 @@ __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
 }
 
 template <int Mode>
-__global__ void __launch_bounds__(kAreaThreads)
+__global__ void __launch_bounds__(kAreaThreads, 3)
     band_area_kernel(Mesh m, const int32_t *__restrict__ band_lo,
                      const int32_t *__restrict__ band_hi, const long long *__restrict__ offsets,
                      double *__restrict__ areas, int64_t cap) {
-    extern __shared__ double s_lat[];
-    const double *lat = m.lat;
+    extern __shared__ double s_lat[];  // L latitudes, then their radii
+    const double *lat = m.lat, *rho_lat = nullptr;
     if (m.L <= kSmemLat) {
-        for (int64_t i = threadIdx.x; i < m.L; i += blockDim.x) s_lat[i] = m.lat[i];
+        for (int64_t i = threadIdx.x; i < m.L; i += blockDim.x) {
+            const double z = m.lat[i];
+            s_lat[i] = z;
+            s_lat[m.L + i] = rho_of_lat(z);
+        }
         __syncthreads();
         lat = s_lat;
+        rho_lat = s_lat + m.L;
     }
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < m.n_faces;
          f += (int64_t)gridDim.x * blockDim.x) {
@@ -303,12 +345,13 @@ __global__ void __launch_bounds__(kAreaThreads)
         for (int64_t i = 0; i < nv; ++i) {
             if (!node_at(m, s + i, a)) break;
             unit(a, ua);
-            if (!(sqrt(fma(ua[0], ua[0], ua[1] * ua[1])) < kPoleRho)) {
+            if (!(fma(ua[0], ua[0], ua[1] * ua[1]) < kPoleRho * kPoleRho)) {
                 st = i;
                 break;
             }
         }
         if (st < 0) continue;
+        Pt pa = make_pt(ua[0], ua[1], ua[2]);
         const double z_st = ua[2];
         double ax = ua[0], ay = ua[1];  // last node off the poles
         double lam_anc = 0.0;           // its unwrapped longitude
@@ -319,27 +362,33 @@ __global__ void __launch_bounds__(kAreaThreads)
             double b[3], ub[3];
             if (!(ok = node_at(m, s + ib, b))) break;
             unit(b, ub);
-            const bool a_pole = sqrt(fma(ua[0], ua[0], ua[1] * ua[1])) < kPoleRho;
-            const bool b_pole = sqrt(fma(ub[0], ub[0], ub[1] * ub[1])) < kPoleRho;
-            // a pole has no longitude: an arc to or from it is a meridian, and
-            // lambda steps from the last node off the poles to the next one
-            const double lam_b = b_pole ? lam_anc : lam_anc + delta_lon(ax, ay, ub[0], ub[1]);
-            if (!(a_pole && b_pole)) {
-                if (!a_pole)
-                    arc_pieces<Mode>(a, b, ua, ub, ua[0], ua[1], lam_anc, lat, m.L, klo, nb, out);
-                else
-                    arc_pieces<Mode>(a, b, ua, ub, ub[0], ub[1], lam_b, lat, m.L, klo, nb, out);
-            }
-            if (!b_pole) {
+            const Pt pb = make_pt(ub[0], ub[1], ub[2]);
+            const bool a_pole = pa.rho == 0.0, b_pole = pb.rho == 0.0;
+            if (a_pole && b_pole) {
+                // nothing: a degenerate or pole-to-pole arc
+            } else if (a_pole) {
+                // a meridian down from the pole: lambda jumps across the pole
+                // from the last node off the poles to b's meridian
+                const double lam_b = lam_anc + delta_lon(ax, ay, ub[0], ub[1]);
+                arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_b, lat, rho_lat, m.L, klo, nb, out);
                 ax = ub[0];
                 ay = ub[1];
                 lam_anc = lam_b;
+            } else {
+                const double d =
+                    arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_anc, lat, rho_lat, m.L, klo, nb, out);
+                if (!b_pole) {
+                    ax = ub[0];
+                    ay = ub[1];
+                    lam_anc += d;
+                }
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 a[c] = b[c];
                 ua[c] = ub[c];
             }
+            pa = pb;
         }
         if (!ok) continue;
         const double w = rint(lam_anc / kTwoPi);
@@ -474,7 +523,7 @@ template <int Mode>
 static cudaError_t launch_areas_mode(const Mesh &m, const int32_t *lo, const int32_t *hi,
                                      const long long *off, double *areas, int64_t cap,
                                      int sm_count, cudaStream_t s) {
-    const size_t smem = m.L <= kSmemLat ? (size_t)m.L * sizeof(double) : 0;
+    const size_t smem = m.L <= kSmemLat ? 2 * (size_t)m.L * sizeof(double) : 0;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, band_area_kernel<Mode>, kAreaThreads, smem);
