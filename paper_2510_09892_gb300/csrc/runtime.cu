@@ -82,6 +82,22 @@ sphx_status ensure_host_staging(sphx_context *ctx, int64_t chunk, cudaStream_t u
     return SPHX_OK;
 }
 
+// true when [p, p + bytes) is page-locked host memory that the device reaches
+// at the same address (unified addressing; on GB300 over NVLink-C2C): both
+// ends of the range are checked
+bool mapped_host(const void *p, size_t bytes) {
+    const char *c = static_cast<const char *>(p);
+    for (const char *q : {c, c + (bytes ? bytes - 1 : 0)}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != q) return false;
+    }
+    return true;
+}
+
 void drop_graphs(sphx_context *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
@@ -430,6 +446,20 @@ sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A,
     if ((int)mode < 0 || (int)mode > 4) return SPHX_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+    if (mapped_host(A, n * 3 * sizeof(double)) && mapped_host(B, n * 3 * sizeof(double)) &&
+        mapped_host(z0, n * sizeof(double)) && mapped_host(out_pts, n * 6 * sizeof(double)) &&
+        mapped_host(out_count, n * sizeof(int32_t))) {
+        // page-locked buffers: the kernel reads the arcs and writes the points
+        // in host memory directly, so the transfers overlap the arithmetic
+        // with no staging copies (one launch on slot stream 0)
+        sphx_status st = ensure_host_staging(ctx, 128, us);
+        if (st != SPHX_OK) return st;
+        HostStaging &h = ctx->host;
+        SPHX_CUDA(cudaEventRecord(h.start, us));
+        SPHX_CUDA(cudaStreamWaitEvent(h.s[0], h.start, 0));
+        return sphx_intersect_gca_constlat(A, B, z0, n, out_pts, out_count, mode,
+                                           reinterpret_cast<sphx_stream>(h.s[0]));
+    }
     int64_t chunk = (n + kHostSlots - 1) / kHostSlots;
     chunk = std::min<int64_t>(kHostMaxChunk, (chunk + 127) / 128 * 128);
     sphx_status st = ensure_host_staging(ctx, chunk, us);
