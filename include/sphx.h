@@ -185,7 +185,9 @@ sphx_status sphx_accux_intermediates(const double *A, const double *B, const dou
    z's and, when the arc passes it, the arc's apex |n_xy| / |n|, Sec. 2),
    widened so that no hit is lost to rounding: by 2^-19 when both endpoints
    have unit norm (the range is then computed in FP32, whose error stays three
-   times below the widening), by 1e-13 otherwise (FP64). lat_z must be sorted
+   times below the widening; for endpoints at most 2^-9 apart from their
+   heights alone, since such an arc rises at most its sagitta, 0.31 |x2 - x1|^2,
+   above them), by 1e-13 otherwise (FP64). lat_z must be sorted
    ascending within each mesh. Sizes as in sphx_intersect_ragged.
    lo, hi: device int32[E]. */
 sphx_status sphx_candidate_ranges(const double *A, const double *B, const int64_t *edge_offsets,

@@ -230,7 +230,7 @@ __device__ __forceinline__ double arc_pieces(const double (&a)[3], const double 
         const Pt p1 = ends[r + 1];
         const double zl = fmin(ends[r].z, p1.z) - kZWiden, zh = fmax(ends[r].z, p1.z) + kZWiden;
         const int64_t j0 = lower_bound_ord(lat, L, ord64(zl));
-        const int64_t j1 = upper_bound_ord(lat, L, ord64(zh));
+        const int64_t j1 = upper_bound_ord_from(lat, L, j0, ord64(zh));
         const int64_t cnt = j1 > j0 ? j1 - j0 : 0;
         const int slot = up ? 0 : 1;
         Pt prev = ends[r];
@@ -287,7 +287,7 @@ __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
                 if (w <= -1.0) zmin = -1.0;
                 if (!(zmax < m.lat[0] || zmin > m.lat[m.L - 1])) {
                     int64_t klo = upper_bound_ord(m.lat, m.L, ord64(zmin)) - 1;
-                    int64_t khi = upper_bound_ord(m.lat, m.L, ord64(zmax)) - 1;
+                    int64_t khi = upper_bound_ord_from(m.lat, m.L, klo + 1, ord64(zmax)) - 1;
                     klo = klo < 0 ? 0 : klo;
                     khi = khi > m.L - 2 ? m.L - 2 : khi;
                     if (khi >= klo) {

@@ -33,10 +33,18 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
                                  int32_t *__restrict__ lo_out, int32_t *__restrict__ hi_out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
          e += (int64_t)gridDim.x * blockDim.x) {
-        // the offsets live on the device and are not validated by the host:
-        // clamp every index derived from them into its buffer
-        int m = (int)upper_bound_dev<int64_t>(edge_offsets, M + 1, e) - 1;
+        // the warp's edges are consecutive and nearly always in one mesh: the
+        // warp's first lane searches, the others step forward past at most the
+        // few mesh boundaries inside the warp's 32 edges. The offsets live on
+        // the device and are not validated by the host: clamp every index
+        // derived from them into its buffer.
+        const unsigned act = __activemask();
+        const int first = __ffs(act) - 1;
+        int m = 0;
+        if ((threadIdx.x & 31) == first) m = (int)upper_bound_dev<int64_t>(edge_offsets, M + 1, e) - 1;
+        m = __shfl_sync(act, m, first);
         m = m < 0 ? 0 : (m >= M ? M - 1 : m);
+        for (int k = 0; k < 32 && m < M - 1 && edge_offsets[m + 1] <= e; ++k) ++m;
         int64_t ls = lat_offsets[m], le = lat_offsets[m + 1];
         ls = ls < 0 ? 0 : (ls > L ? L : ls);
         le = le < ls ? ls : (le > L ? L : le);
@@ -48,8 +56,9 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
                             finite_bits(x2[0]) && finite_bits(x2[1]) && finite_bits(x2[2]);
         if (finite && (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
             const double *lz = lat_z + ls;
-            lo = (int32_t)(ls + lower_bound_ord(lz, le - ls, ord64(zmin)));
-            hi = (int32_t)(ls + upper_bound_ord(lz, le - ls, ord64(zmax)));
+            const int64_t l = lower_bound_ord(lz, le - ls, ord64(zmin));
+            lo = (int32_t)(ls + l);
+            hi = (int32_t)(ls + upper_bound_ord_from(lz, le - ls, l, ord64(zmax)));
             if (hi < lo) hi = lo;
         }
         lo_out[e] = lo;

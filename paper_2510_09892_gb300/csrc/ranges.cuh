@@ -54,6 +54,29 @@ __device__ __forceinline__ int64_t upper_bound_ord(const double *a, int64_t n, l
     return lo;
 }
 
+// first index i in [from, n) with a[i] > key (by ord64), found by galloping
+// forward from `from` (steps 1, 2, 4, ... then a binary search): a few loads
+// when the answer is near `from`, as for the short ranges of latitudes an arc
+// spans
+__device__ __forceinline__ int64_t upper_bound_ord_from(const double *a, int64_t n, int64_t from,
+                                                        long long key) {
+    int64_t lo = from, hi = from, step = 1;
+    while (hi < n && ord64(a[hi]) <= key) {
+        lo = hi + 1;
+        hi += step;
+        step <<= 1;
+    }
+    if (hi > n) hi = n;
+    while (lo < hi) {  // a[lo - 1] <= key (or lo == from); a[hi] > key or hi == n
+        const int64_t mid = (lo + hi) >> 1;
+        if (ord64(a[mid]) > key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 // a float in [-2, 2] as a double, by its bits (values below 2^-126 become +-0)
 __device__ __forceinline__ double f64_of_f32_small(float f) {
     const uint32_t b = wide::fbits_of(f);
@@ -123,6 +146,16 @@ __device__ __forceinline__ bool z_range_fp64(const double (&x1)[3], const double
 // endpoints, or |n| below the FP32 range).
 constexpr float kZWiden32 = 1.0f / (1 << 19);
 
+//
+// Short arcs take a shorter path: a circular arc stays within its sagitta
+// 1 - cos(L/2) <= L^2 / 8 of its chord, so its heights exceed the endpoints'
+// by at most that; with the chord |x2 - x1| <= 2^-9 (from FP32 differences,
+// within 2.2e-6 of the exact one for endpoints of norm 1 +- 1e-6), L^2 / 8 <=
+// 0.31 |x2 - x1|^2 < 1.2e-6, and with the endpoints' FP32 heights (error below
+// 2.5e-7) the same widening 2^-19 = 1.9e-6 covers it: no cross product, no
+// apex test and no FP64 difference are needed.
+constexpr float kShortChord2 = 1.0f / (1 << 18);
+
 __device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
                                              double &zmin, double &zmax) {
     float p1[3], p2[3];
@@ -134,6 +167,15 @@ __device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double
     const float q1 = p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2];
     const float q2 = p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2];
     if (!(fabsf(q1 - 1.0f) < 1e-6f && fabsf(q2 - 1.0f) < 1e-6f)) return false;
+    {
+        const float dx = p2[0] - p1[0], dy = p2[1] - p1[1], dz = p2[2] - p1[2];
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= kShortChord2) {
+            const float z1 = p1[2] * rsqrtf(q1), z2 = p2[2] * rsqrtf(q2);
+            zmin = f64_of_f32_small(fminf(z1, z2) - kZWiden32);
+            zmax = f64_of_f32_small(fmaxf(z1, z2) + kZWiden32);
+            return true;
+        }
+    }
     const double sg = (p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f) ? 1.0 : -1.0;
     float d[3];
 #pragma unroll
