@@ -608,7 +608,29 @@ def cpu_baseline_leg() -> dict:
         oracle_rate(A[:1024], B[:1024], z[:1024], pool)  # start the workers
         rate = oracle_rate(A[:n], B[:n], z[:n], pool)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} arcs of the 10^6-arc stress workload"}
+            "sample": f"first {n} arcs of the 10^6-arc stress workload",
+            "step_reference": step_reference_rates(A, B, z)}
+
+
+def step_reference_rates(A, B, z) -> dict:
+    """The paper's two FP64 forms as scalar C on one host core (the step
+    reference, gcc -O2 -ffp-contract=off): direct Eq. 2.2 and AccuX
+    (Algorithm 8), over the whole 10^6-arc stress workload. The paper reports
+    AccuX about 9x slower than the direct form serially (Sec. 8)."""
+    from oracle import steps
+    steps.lib()  # build outside the timing
+    out = {}
+    for name, fn in (("direct", lambda: steps.direct(A, B, z)),
+                     ("accux", lambda: steps.accux(A, B, z, variant=2))):
+        best = float("inf")
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            best = min(best, time.perf_counter() - t0)
+        out[name] = {"value": len(z) / best, "unit": UNIT, "cores": 1}
+    out["accux_over_direct_time"] = out["direct"]["value"] / out["accux"]["value"]
+    out["sample"] = "the whole 10^6-arc stress workload, one core, best of 3"
+    return out
 
 
 def e2e_leg(sphx, torch, dev, A, B, z, args, mode) -> dict:
