@@ -267,3 +267,28 @@ def test_full_size_cubed_sphere(ctx):
         got = np.zeros(nb)
         got[loh[f]:hih[f]] = Ah[aoh[f]:aoh[f + 1]]
         assert np.abs(got - ref[i]).max() <= tol[i], (f, np.abs(got - ref[i]).max(), tol[i])
+
+
+def test_many_latitudes_global_paths(ctx):
+    """More latitudes than the kernels stage in shared memory: the area kernel
+    reads them (and computes their radii) from global memory, and the zonal
+    sums accumulate in global memory (3500 bands)."""
+    nodes, off, fn = W.polygon_cells(40, seed=34, radius=(1e-3, 0.3))
+    cells = W.cells_as_lists(nodes, off, fn)
+    lat = np.concatenate([[-1.0], np.sort(np.random.default_rng(8).uniform(-1, 1, 3499)), [1.0]])
+    check_against_oracle(ctx, cells, lat, modes=("wide",))
+    lo, hi, ao, A = sphx.band_areas(ctx, dev(nodes), dev(off), dev(fn), dev(lat), "wide")
+    F, nb = len(off) - 1, len(lat) - 1
+    field = dev(np.arange(F, dtype=np.float64))
+    fa = torch.empty(nb, dtype=torch.float64, device=DEV)
+    aa = torch.empty(nb, dtype=torch.float64, device=DEV)
+    sphx.sphx_zonal_sums(ctx, lo, hi, ao, A, field, len(lat), fa, aa)
+    assert ctx.sync_status() == sphx.OK
+    lo, hi, ao, A = (t.cpu().numpy() for t in (lo, hi, ao, A))
+    want_a = np.zeros(nb)
+    want_fa = np.zeros(nb)
+    for f in range(F):
+        want_a[lo[f]:hi[f]] += A[ao[f]:ao[f + 1]]
+        want_fa[lo[f]:hi[f]] += f * A[ao[f]:ao[f + 1]]
+    np.testing.assert_allclose(aa.cpu().numpy(), want_a, rtol=1e-14, atol=1e-300)
+    np.testing.assert_allclose(fa.cpu().numpy(), want_fa, rtol=1e-14, atol=1e-300)
