@@ -341,3 +341,37 @@ def test_reflection_equivariance_on_gpu(mode, axis):
         c1, p1 = run(*_reflect(A, B, z, axis), mode)
     assert np.array_equal(c0, c1)
     assert equal_as_mapped(c0, p1, expected_after(p0, axis))
+
+
+def test_error_distribution_report():
+    """Error distributions against the exact oracle, per mode and workload
+    (printed; run with -s to see them): the fraction of coordinates that are
+    correctly rounded, and the median / p95 / p99 / max of the component
+    error in the gate's units (ulp for large components, u sqrt(1 - z0^2) for
+    small ones), over unflagged arcs. Bounds: integer limbs <= 1, FP64-EFT
+    <= 4; direct FP64 loses many digits on the stress mix (Sec. 4)."""
+    rows = []
+    for name, (A, B, z) in (("uniform", W.uniform_arcs(20_000, seed=14)),
+                            ("stress", W.stress_arcs(20_000, seed=13))):
+        ce, pe, fe = P.run_exact(A, B, z)
+        ok = fe == 0
+        for mode in ("wide", "eft", "direct", "ff32"):
+            cnt, pts = run(A, B, z, mode)
+            both = ok[:, None] & np.isfinite(pe[..., 0]) & np.isfinite(pts[..., 0])
+            ulp, _, gate = P.component_errors(pts, pe, z)
+            g = gate[both]
+            exact_frac = float(np.mean(ulp[both] == 0.0))
+            q = np.percentile(g, [50, 95, 99])
+            counts_equal = float(np.mean(cnt[ok] == ce[ok]))
+            rows.append((name, mode, exact_frac, q[0], q[1], q[2], float(g.max()), counts_equal))
+            if mode == "wide":
+                assert g.max() <= 1.0 and exact_frac > 0.999
+            if mode == "eft":
+                assert g.max() <= 4.0
+            if mode == "direct" and name == "stress":
+                assert g.max() > 100.0
+            if mode in ("wide", "eft"):
+                assert counts_equal == 1.0
+    print("\nworkload  mode    correctly-rounded  p50     p95     p99     max        counts")
+    for r in rows:
+        print(f"{r[0]:9s} {r[1]:7s} {r[2]:17.6f}  {r[3]:.3g}  {r[4]:.3g}  {r[5]:.3g}  {r[6]:.4g}  {r[7]:.6f}")
