@@ -22,10 +22,6 @@ from tests import parity as P
 
 pytestmark = pytest.mark.gpu
 
-# float-float's stated bound (s^2 carries about 46 bits, so its absolute error
-# near 2^-46 |n|^2 is amplified by 1 / (2 s) near tangency and near the poles):
-#   |P~ - P| <= 2^-44 sqrt(1 - z0^2) + 2^-45 |n|^2 / (|n_xy| s)
-FF_RHO, FF_COND = 2.0 ** -44, 2.0 ** -45
 
 
 def run(A, B, z, mode):
@@ -133,18 +129,6 @@ def test_wide_int_full_size_stress_sampled():
     assert np.nanmax(np.where(both[..., None], gate, 0)) <= 5.0
 
 
-def _ff_bound(A, B, z):
-    """Stated float-float bound in units of u sqrt(1 - z0^2) (the norm_error unit)."""
-    n = np.cross(A, B)
-    nxy = np.hypot(n[:, 0], n[:, 1])
-    S3 = (n ** 2).sum(1)
-    s = np.sqrt(np.maximum(nxy ** 2 - S3 * z * z, 0))
-    rho = np.sqrt(np.maximum(0.0, (1 - z) * (1 + z)))
-    with np.errstate(divide="ignore"):
-        b = FF_RHO * rho + FF_COND * S3 / (nxy * s)
-    return b / (P.U * np.maximum(rho, 1e-300))
-
-
 @pytest.mark.parametrize("gen", ["uniform", "stress"])
 def test_ff32_within_stated_bound(gen):
     if gen == "uniform":
@@ -154,7 +138,7 @@ def test_ff32_within_stated_bound(gen):
     cnt, pts = run(A, B, z, "ff32")
     ce, pe, fe = P.run_exact(A, B, z)
     ok = fe == 0
-    bound = _ff_bound(A, B, z)
+    bound = P.ff_bound(A, B, z)
     hit = np.isfinite(pe[..., 0]) & np.isfinite(pts[..., 0]) & ok[:, None]
     err = P.norm_error(pts, pe, z)
     assert (np.where(hit, err, 0) <= bound[:, None]).all()
