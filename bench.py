@@ -441,7 +441,7 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
            "edges": E, "candidate_pairs": pairs, "modes": {}}
     cur = torch.cuda.current_stream(dev)
     with sphx.Context(dev.index or 0) as ctx:
-        for mode in (head, "eft"):
+        for mode in (head, "eft", "direct"):
             for _ in range(args.warmup):
                 sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
                                            total, mode, stream=cur)
@@ -529,7 +529,8 @@ def meshes_leg(sphx, torch, dev, args, head, pool) -> dict:
     """Ragged batching (not the headline): 512 independent polygon meshes of
     10^3 - 5x10^6 edges (log-uniform, ~3x10^8 edges in all) against per-mesh
     grids of 180 - 2881 latitudes, in one persistent launch replayed from a
-    CUDA graph, with the launch shape picked by sphx_autotune_ragged."""
+    CUDA graph, with the launch shape picked by sphx_autotune_ragged; integer
+    limbs, FP64-EFT and direct FP64."""
     E, L = W.ragged_sizes(512, 1e3, 5e6)
     eo = np.concatenate([[0], np.cumsum(E)]).astype(np.int64)
     lo_ = np.concatenate([[0], np.cumsum(L)]).astype(np.int64)
@@ -558,7 +559,7 @@ def meshes_leg(sphx, torch, dev, args, head, pool) -> dict:
                        "latitudes per mesh", "edges": Et, "candidate_pairs": pairs, "modes": {}}
     cur = torch.cuda.current_stream(dev)
     with sphx.Context(dev.index or 0) as ctx:
-        for mode in (head, "eft"):
+        for mode in (head, "eft", "direct"):
             ctx.reset_tuning()
             tune_ms = sphx.sphx_autotune_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
                                                 stream=cur)
