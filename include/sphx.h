@@ -243,7 +243,8 @@ sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const doub
    around a pole), and area_offsets (device int64[n_faces + 1]), the exclusive
    prefix sum of band_hi - band_lo: the area of cell f in band k goes to
    areas[area_offsets[f] + k - band_lo[f]], and area_offsets[n_faces] is the
-   number of entries. Scratch for the prefix sum comes from ctx. Stream
+   number of entries. Scratch for the prefix sum comes from ctx: calls on one
+   context must not overlap in time (as for sphx_intersect_ragged). Stream
    ordered. */
 sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, int64_t n_nodes,
                              const int64_t *face_offsets, const int32_t *face_nodes,
@@ -281,8 +282,10 @@ sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, int64_t n_no
    point, so the sums do not depend on the order the GPU adds them in
    (bitwise reproducible); the results are the exact sums rounded to FP64.
    Terms of magnitude 2^46 or more, or non-finite, are left out and
-   sphx_sync_status() reports SPHX_ERR_INVALID_ARG. Scratch comes from ctx.
-   Stream ordered. */
+   sphx_sync_status() reports SPHX_ERR_INVALID_ARG. band_lo, band_hi,
+   area_offsets and areas are those sphx_band_ranges and sphx_band_areas
+   wrote (the call reads areas where the offsets point). Scratch comes from
+   ctx: calls on one context must not overlap in time. Stream ordered. */
 sphx_status sphx_zonal_sums(sphx_context *ctx, const int32_t *band_lo, const int32_t *band_hi,
                             const int64_t *area_offsets, int64_t n_faces, const double *areas,
                             const double *field, int64_t n_lat, double *out_fa, double *out_a,

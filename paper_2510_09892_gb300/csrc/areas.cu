@@ -578,6 +578,7 @@ extern "C" sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, 
         !area_offsets || (n_faces > 0 && (!band_lo || !band_hi)))
         return SPHX_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> g(ctx->mu);
     SPHX_CUDA(cudaSetDevice(ctx->device));
     if (n_faces == 0) {
         SPHX_CUDA(cudaMemsetAsync(area_offsets, 0, sizeof(int64_t), s));
@@ -652,6 +653,7 @@ extern "C" sphx_status sphx_zonal_sums(sphx_context *ctx, const int32_t *band_lo
         return SPHX_ERR_INVALID_ARG;
     const int64_t n_bands = n_lat - 1;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> g(ctx->mu);
     SPHX_CUDA(cudaSetDevice(ctx->device));
     sphx_status st = ensure_zonal_scratch(ctx, n_bands);
     if (st != SPHX_OK) return st;
