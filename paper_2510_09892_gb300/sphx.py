@@ -410,6 +410,21 @@ def band_areas(ctx: Context, nodes, face_offsets, face_nodes, lat_z, mode="wide"
     return band_lo, band_hi, off, areas[:total]
 
 
+def zonal_sums(ctx: Context, nodes, face_offsets, face_nodes, lat_z, field, mode="wide",
+               stream=None):
+    """The whole zonal-mean step in one call: band ranges, band areas and the
+    per-band sums. Returns (sum of field * area, sum of area) per band as
+    float64 CUDA tensors of n_lat - 1 entries; their ratio is the zonal mean."""
+    lo, hi, off, areas = band_areas(ctx, nodes, face_offsets, face_nodes, lat_z, mode, stream)
+    nb = int(lat_z.numel()) - 1
+    fa = torch.empty(nb, dtype=torch.float64, device=nodes.device)
+    aa = torch.empty(nb, dtype=torch.float64, device=nodes.device)
+    if areas.numel() == 0:  # no cell meets any band
+        areas = torch.zeros(1, dtype=torch.float64, device=nodes.device)
+    sphx_zonal_sums(ctx, lo, hi, off, areas, field, int(lat_z.numel()), fa, aa, stream)
+    return fa, aa
+
+
 def hits_to_numpy(out, total: int):
     """View the first `total` records of a ragged output buffer as a numpy structured array."""
     import numpy as np

@@ -292,3 +292,19 @@ def test_many_latitudes_global_paths(ctx):
         want_fa[lo[f]:hi[f]] += f * A[ao[f]:ao[f + 1]]
     np.testing.assert_allclose(aa.cpu().numpy(), want_a, rtol=1e-14, atol=1e-300)
     np.testing.assert_allclose(fa.cpu().numpy(), want_fa, rtol=1e-14, atol=1e-300)
+
+
+def test_one_call_zonal_sums(ctx):
+    """sphx.zonal_sums (ranges + areas + sums in one call) equals the three
+    calls made by hand, bit for bit, and its band totals are 2 pi dz."""
+    nodes, off, fn = W.cubed_sphere_cells(16)
+    lat = W.latlon_latitudes(37)
+    field = dev(np.random.default_rng(9).standard_normal(len(off) - 1))
+    fa, aa = sphx.zonal_sums(ctx, dev(nodes), dev(off), dev(fn), dev(lat), field)
+    lo, hi, ao, A = sphx.band_areas(ctx, dev(nodes), dev(off), dev(fn), dev(lat), "wide")
+    fa2 = torch.empty_like(fa)
+    aa2 = torch.empty_like(aa)
+    sphx.sphx_zonal_sums(ctx, lo, hi, ao, A, field, len(lat), fa2, aa2)
+    assert ctx.sync_status() == sphx.OK
+    assert torch.equal(fa, fa2) and torch.equal(aa, aa2)
+    np.testing.assert_allclose(aa.cpu().numpy(), TWO_PI * np.diff(lat), rtol=0, atol=1e-14)
