@@ -218,17 +218,23 @@ def main():
                     help="headline evaluation mode (the others are timed beside it)")
     ap.add_argument("--zonal-only", action="store_true",
                     help="run only the zonal-mean leg and print its JSON (for profiling)")
+    ap.add_argument("--ragged-only", action="store_true",
+                    help="run only the cubed-sphere regridding leg and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
-    if args.zonal_only:
+    if args.zonal_only or args.ragged_only:
         import torch
         from paper_2510_09892_gb300 import sphx
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        print(json.dumps({"zonal_mean": zonal_leg(sphx, torch, dev, args, args.mode)}), flush=True)
+        if args.zonal_only:
+            line = {"zonal_mean": zonal_leg(sphx, torch, dev, args, args.mode)}
+        else:
+            line = {"ragged_regridding": ragged_leg(sphx, torch, dev, args, args.mode)}
+        print(json.dumps(line), flush=True)
         return
 
     rank, world, local = dist_env()
@@ -422,7 +428,8 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
     the 721 latitudes of a 0.25-degree grid. One step is the whole ragged
     sequence (candidate ranges, prefix sum, persistent intersection with
     compaction), replayed from the context's CUDA graph; the 605 MB of edges
-    exceed L2, so no flush is needed."""
+    exceed L2, so no flush is needed. The launch shape is picked by
+    sphx_autotune_ragged for each mode first."""
     A, B = W.cubed_sphere_edges(1024)
     lat = W.latlon_latitudes(721)
     E = len(A)
@@ -442,6 +449,9 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
     cur = torch.cuda.current_stream(dev)
     with sphx.Context(dev.index or 0) as ctx:
         for mode in (head, "eft", "direct"):
+            ctx.reset_tuning()
+            tune_ms = sphx.sphx_autotune_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
+                                                total, mode, stream=cur)
             for _ in range(args.warmup):
                 sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
                                            total, mode, stream=cur)
@@ -461,7 +471,8 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
             res["modes"][mode] = {
                 "ms_per_step": ms, "edges_per_s": E / (ms * 1e-3),
                 "pairs_per_s": pairs / (ms * 1e-3), "hits_per_s": hits / (ms * 1e-3),
-                "hbm_frac": (48 * E + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak()}
+                "hbm_frac": (48 * E + 32 * hits) / (ms * 1e-3) / 1e9 / measured_hbm_peak(),
+                "tuning": ctx.get_tuning(), "autotune_best_ms": tune_ms}
     return res
 
 

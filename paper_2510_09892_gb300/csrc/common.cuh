@@ -33,10 +33,10 @@ void set_cuda_error(cudaError_t e);
     } while (0)
 
 // launch shape of the ragged intersection kernel
-struct RaggedShape {
+struct RaggedShape {  // defaults: what the autotuner picks on both GB300 workloads
     int threads = 256;
-    int blocks_per_sm = 4;
-    int pairs_per_lane = 2;
+    int blocks_per_sm = 8;
+    int pairs_per_lane = 1;
     int compaction = SPHX_COMPACT_ATOMIC;
     int use_graph = 1;
     bool operator<(const RaggedShape &o) const {
