@@ -35,6 +35,10 @@
 //                        the slot-1 hits of descending ones, an arc that
 //                        passes its highest (lowest) point being split there
 //                        into a rising and a falling run.
+//     Cells that lie inside one band (most, when cells are smaller than
+//     bands) take a shorter path: band_partition_kernel sorts the cells into
+//     two lists, and fan_area_kernel gives each one-band cell its own area,
+//     a fan of spherical triangles (Van Oosterom and Strackee's excess).
 //  3. zonal_sum_kernel   per band, sum of field * area and of area, in 128-bit
 //                        fixed point with 64-bit integer atomics (per block in
 //                        shared memory, then once per block in global memory),
@@ -302,11 +306,214 @@ __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
     }
 }
 
+// The area of cell f in each band of its range by the boundary integral
+// (Green's theorem in longitude and height, see add_piece and arc_pieces)
+template <int Mode>
+__device__ __forceinline__ void green_cell(const Mesh &m, int64_t f,
+                                           const int32_t *__restrict__ band_lo,
+                                           const int32_t *__restrict__ band_hi,
+                                           const long long *__restrict__ offsets,
+                                           double *__restrict__ areas, int64_t cap,
+                                           const double *lat, const double *rho_lat) {
+    const int64_t klo = band_lo[f];
+    const int64_t nb = (int64_t)band_hi[f] - klo;
+    if (nb <= 0) return;
+    if (klo < 0 || klo + nb > m.L - 1) {
+        atomicOr(m.status, kStatusInvalid);
+        return;
+    }
+    const long long off = offsets[f];
+    if (off < 0 || off + nb > cap) {
+        atomicOr(m.status, kStatusCapacity);
+        return;
+    }
+    double *out = areas + off;
+    for (int64_t j = 0; j < nb; ++j) out[j] = 0.0;
+    int64_t s, e;
+    if (!cell_span(m, f, s, e) || e - s < 2) return;
+    const int64_t nv = e - s;
+    // the first node off the poles: lambda = 0 there, and the cut to a
+    // pole inside the cell starts there
+    int64_t st = -1;
+    double a[3], ua[3];
+    for (int64_t i = 0; i < nv; ++i) {
+        if (!node_at(m, s + i, a)) break;
+        unit(a, ua);
+        if (!(fma(ua[0], ua[0], ua[1] * ua[1]) < kPoleRho * kPoleRho)) {
+            st = i;
+            break;
+        }
+    }
+    if (st < 0) return;
+    Pt pa = make_pt(ua[0], ua[1], ua[2]);
+    const double z_st = ua[2];
+    double ax = ua[0], ay = ua[1];  // last node off the poles
+    double lam_anc = 0.0;           // its unwrapped longitude
+    bool ok = true;
+    for (int64_t t = 0; t < nv; ++t) {
+        int64_t ib = st + t + 1;
+        if (ib >= nv) ib -= nv;
+        double b[3], ub[3];
+        if (!(ok = node_at(m, s + ib, b))) break;
+        unit(b, ub);
+        const Pt pb = make_pt(ub[0], ub[1], ub[2]);
+        const bool a_pole = pa.rho == 0.0, b_pole = pb.rho == 0.0;
+        if (a_pole && b_pole) {
+            // nothing: a degenerate or pole-to-pole arc
+        } else if (a_pole) {
+            // a meridian down from the pole: lambda jumps across the pole
+            // from the last node off the poles to b's meridian
+            const double lam_b = lam_anc + delta_lon(ax, ay, ub[0], ub[1]);
+            arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_b, lat, rho_lat, m.L, klo, nb, out);
+            ax = ub[0];
+            ay = ub[1];
+            lam_anc = lam_b;
+        } else {
+            const double d =
+                arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_anc, lat, rho_lat, m.L, klo, nb, out);
+            if (!b_pole) {
+                ax = ub[0];
+                ay = ub[1];
+                lam_anc += d;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c] = b[c];
+            ua[c] = ub[c];
+        }
+        pa = pb;
+    }
+    if (!ok) return;
+    const double w = rint(lam_anc / kTwoPi);
+    if (w != 0.0) {
+        for (int64_t j = 0; j < nb; ++j) {
+            const double zl = lat[klo + j], zh = lat[klo + j + 1];
+            const double lo = w > 0.0 ? fmax(zl, z_st) : fmax(zl, -1.0);
+            const double hi = w > 0.0 ? fmin(zh, 1.0) : fmin(zh, z_st);
+            if (hi > lo) out[j] += kTwoPi * (hi - lo);
+        }
+    }
+}
+
+// Cells are split in two lists (warp-aggregated appends, so warps stay
+// uniform): cells that lie inside one band other than the first and the last
+// (their widened height range is, so nothing was clamped), whose band area is
+// the cell's own area, and the others.
+__global__ void band_partition_kernel(const int32_t *__restrict__ band_lo,
+                                      const int32_t *__restrict__ band_hi, int64_t F, int64_t L,
+                                      int32_t *__restrict__ lists, unsigned long long *counts) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < F;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = base + lane;
+        int64_t klo = 0, nb = 0;
+        if (f < F) {
+            klo = band_lo[f];
+            nb = (int64_t)band_hi[f] - klo;
+        }
+        const bool one = f < F && nb == 1 && klo > 0 && klo < L - 2;
+        const bool other = f < F && nb > 0 && !one;
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const bool mine = w == 0 ? one : other;
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (!bal) continue;
+            unsigned long long at = 0;
+            if (lane == __ffs(bal) - 1) at = atomicAdd(counts + w, (unsigned long long)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, __ffs(bal) - 1);
+            if (mine) lists[w * F + (int64_t)at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)f;
+        }
+    }
+}
+
+// The area of a cell that lies inside one band, written to its one band
+// entry: the sum of its fan triangles' spherical excesses from node 0, each by
+// Van Oosterom and Strackee, tan(E / 2) = a . (b x c) / (1 + a.b + b.c + c.a),
+// with the triple product taken as a . ((b - a) x (c - a)) so that small
+// triangles keep relative accuracy (atan by its series below 2^-9). Returns
+// true, writing nothing, when a node is more than 60 degrees from node 0: the
+// fan is not used for such a cell.
+__device__ __forceinline__ bool fan_area(const Mesh &m, int64_t f,
+                                         const long long *__restrict__ offsets,
+                                         double *__restrict__ areas, int64_t cap) {
+    {
+        const long long off = offsets[f];
+        if (off < 0 || off + 1 > cap) {
+            atomicOr(m.status, kStatusCapacity);
+            return false;
+        }
+        int64_t s, e;
+        if (!cell_span(m, f, s, e)) return false;
+        double v0[3], a[3], b[3], u[3];
+        double area = 0.0;
+        bool ok = true, far = false;
+        if (e - s >= 3) {
+            ok = node_at(m, s, u);
+            unit(u, v0);
+            if (ok) ok = node_at(m, s + 1, u);
+            unit(u, a);
+            far = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2])) < 0.5;
+            for (int64_t j = s + 2; j < e && ok && !far; ++j) {
+                if (!(ok = node_at(m, j, u))) break;
+                unit(u, b);
+                const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+                const double ob = fma(v0[0], b[0], fma(v0[1], b[1], v0[2] * b[2]));
+                const double oa = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2]));
+                far = ob < 0.5;
+                const double d1x = a[0] - v0[0], d1y = a[1] - v0[1], d1z = a[2] - v0[2];
+                const double d2x = b[0] - v0[0], d2y = b[1] - v0[1], d2z = b[2] - v0[2];
+                const double tri = fma(v0[0], d1y * d2z - d1z * d2y,
+                                       fma(v0[1], d1z * d2x - d1x * d2z,
+                                           v0[2] * (d1x * d2y - d1y * d2x)));
+                const double t = tri / (1.0 + oa + ab + ob);
+                area += 2.0 * (fabs(t) <= 0.001953125 ? atan_small(t) : atan(t));
+                a[0] = b[0];
+                a[1] = b[1];
+                a[2] = b[2];
+            }
+        }
+        if (!ok) return false;
+        if (far) return true;
+        areas[off] = area;
+        return false;
+    }
+}
+
+// fan_area over the one-band list; a cell the fan does not take is appended
+// to the other list, which band_area_kernel (launched after this kernel)
+// works through
+__global__ void __launch_bounds__(kAreaThreads, 8)
+    fan_area_kernel(Mesh m, const long long *__restrict__ offsets, double *__restrict__ areas,
+                    int64_t cap, int32_t *__restrict__ lists,
+                    unsigned long long *__restrict__ counts) {
+    const int64_t n = (int64_t)counts[0];
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + lane;
+        bool far = false;
+        int64_t f = -1;
+        if (i < n) {
+            f = lists[i];
+            far = fan_area(m, f, offsets, areas, cap);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, far);
+        if (bal) {
+            unsigned long long at = 0;
+            if (lane == __ffs(bal) - 1) at = atomicAdd(counts + 1, (unsigned long long)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, __ffs(bal) - 1);
+            if (far) lists[m.n_faces + (int64_t)at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)f;
+        }
+    }
+}
+
 template <int Mode>
 __global__ void __launch_bounds__(kAreaThreads, 3)
     band_area_kernel(Mesh m, const int32_t *__restrict__ band_lo,
                      const int32_t *__restrict__ band_hi, const long long *__restrict__ offsets,
-                     double *__restrict__ areas, int64_t cap) {
+                     double *__restrict__ areas, int64_t cap, const int32_t *__restrict__ list,
+                     const unsigned long long *__restrict__ count) {
     extern __shared__ double s_lat[];  // L latitudes, then their radii
     const double *lat = m.lat, *rho_lat = nullptr;
     if (m.L <= kSmemLat) {
@@ -319,88 +526,10 @@ __global__ void __launch_bounds__(kAreaThreads, 3)
         lat = s_lat;
         rho_lat = s_lat + m.L;
     }
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < m.n_faces;
-         f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t klo = band_lo[f];
-        const int64_t nb = (int64_t)band_hi[f] - klo;
-        if (nb <= 0) continue;
-        if (klo < 0 || klo + nb > m.L - 1) {
-            atomicOr(m.status, kStatusInvalid);
-            continue;
-        }
-        const long long off = offsets[f];
-        if (off < 0 || off + nb > cap) {
-            atomicOr(m.status, kStatusCapacity);
-            continue;
-        }
-        double *out = areas + off;
-        for (int64_t j = 0; j < nb; ++j) out[j] = 0.0;
-        int64_t s, e;
-        if (!cell_span(m, f, s, e) || e - s < 2) continue;
-        const int64_t nv = e - s;
-        // the first node off the poles: lambda = 0 there, and the cut to a
-        // pole inside the cell starts there
-        int64_t st = -1;
-        double a[3], ua[3];
-        for (int64_t i = 0; i < nv; ++i) {
-            if (!node_at(m, s + i, a)) break;
-            unit(a, ua);
-            if (!(fma(ua[0], ua[0], ua[1] * ua[1]) < kPoleRho * kPoleRho)) {
-                st = i;
-                break;
-            }
-        }
-        if (st < 0) continue;
-        Pt pa = make_pt(ua[0], ua[1], ua[2]);
-        const double z_st = ua[2];
-        double ax = ua[0], ay = ua[1];  // last node off the poles
-        double lam_anc = 0.0;           // its unwrapped longitude
-        bool ok = true;
-        for (int64_t t = 0; t < nv; ++t) {
-            int64_t ib = st + t + 1;
-            if (ib >= nv) ib -= nv;
-            double b[3], ub[3];
-            if (!(ok = node_at(m, s + ib, b))) break;
-            unit(b, ub);
-            const Pt pb = make_pt(ub[0], ub[1], ub[2]);
-            const bool a_pole = pa.rho == 0.0, b_pole = pb.rho == 0.0;
-            if (a_pole && b_pole) {
-                // nothing: a degenerate or pole-to-pole arc
-            } else if (a_pole) {
-                // a meridian down from the pole: lambda jumps across the pole
-                // from the last node off the poles to b's meridian
-                const double lam_b = lam_anc + delta_lon(ax, ay, ub[0], ub[1]);
-                arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_b, lat, rho_lat, m.L, klo, nb, out);
-                ax = ub[0];
-                ay = ub[1];
-                lam_anc = lam_b;
-            } else {
-                const double d =
-                    arc_pieces<Mode>(a, b, ua, ub, pa, pb, lam_anc, lat, rho_lat, m.L, klo, nb, out);
-                if (!b_pole) {
-                    ax = ub[0];
-                    ay = ub[1];
-                    lam_anc += d;
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                a[c] = b[c];
-                ua[c] = ub[c];
-            }
-            pa = pb;
-        }
-        if (!ok) continue;
-        const double w = rint(lam_anc / kTwoPi);
-        if (w != 0.0) {
-            for (int64_t j = 0; j < nb; ++j) {
-                const double zl = lat[klo + j], zh = lat[klo + j + 1];
-                const double lo = w > 0.0 ? fmax(zl, z_st) : fmax(zl, -1.0);
-                const double hi = w > 0.0 ? fmin(zh, 1.0) : fmin(zh, z_st);
-                if (hi > lo) out[j] += kTwoPi * (hi - lo);
-            }
-        }
-    }
+    const int64_t n = (int64_t)*count;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        green_cell<Mode>(m, list[i], band_lo, band_hi, offsets, areas, cap, lat, rho_lat);
 }
 
 // ---- zonal sums in 128-bit fixed point ---------------------------------------------
@@ -522,16 +651,29 @@ __global__ void zonal_finish_kernel(const unsigned long long *__restrict__ acc, 
 template <int Mode>
 static cudaError_t launch_areas_mode(const Mesh &m, const int32_t *lo, const int32_t *hi,
                                      const long long *off, double *areas, int64_t cap,
-                                     int sm_count, cudaStream_t s) {
-    const size_t smem = m.L <= kSmemLat ? 2 * (size_t)m.L * sizeof(double) : 0;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, band_area_kernel<Mode>, kAreaThreads, smem);
+                                     int32_t *lists, unsigned long long *counts, int sm_count,
+                                     cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t need = (m.n_faces + kAreaThreads - 1) / kAreaThreads;
-    const int64_t grid = std::min<int64_t>(need, (int64_t)per_sm * sm_count);
-    band_area_kernel<Mode><<<(unsigned)grid, kAreaThreads, smem, s>>>(m, lo, hi, off, areas, cap);
+    const int64_t need = (m.n_faces + 255) / 256;
+    band_partition_kernel<<<(unsigned)std::min<int64_t>(need, (int64_t)sm_count * 8), 256, 0, s>>>(
+        lo, hi, m.n_faces, m.L, lists, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fan_area_kernel, kAreaThreads, 0);
+    if (e != cudaSuccess) return e;
+    int64_t grid = std::min<int64_t>((m.n_faces + kAreaThreads - 1) / kAreaThreads,
+                                     (int64_t)std::max(per_sm, 1) * sm_count);
+    fan_area_kernel<<<(unsigned)grid, kAreaThreads, 0, s>>>(m, off, areas, cap, lists, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = m.L <= kSmemLat ? 2 * (size_t)m.L * sizeof(double) : 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_area_kernel<Mode>, kAreaThreads,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    grid = std::min<int64_t>((m.n_faces + kAreaThreads - 1) / kAreaThreads,
+                             (int64_t)std::max(per_sm, 1) * sm_count);
+    band_area_kernel<Mode><<<(unsigned)grid, kAreaThreads, smem, s>>>(
+        m, lo, hi, off, areas, cap, lists + m.n_faces, counts + 1);
     return cudaGetLastError();
 }
 
@@ -610,31 +752,34 @@ extern "C" sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, i
         return SPHX_ERR_INVALID_ARG;
     if (n_faces == 0) return SPHX_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> g(ctx->mu);
     SPHX_CUDA(cudaSetDevice(ctx->device));
+    sphx_status st = ensure_band_scratch(ctx, n_faces);
+    if (st != SPHX_OK) return st;
     const Mesh m =
         make_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z, n_lat);
     const long long *off = reinterpret_cast<const long long *>(area_offsets);
     cudaError_t e;
     switch (mode) {
         case SPHX_MODE_DIRECT_FP64:
-            e = launch_areas_mode<kDirect>(m, band_lo, band_hi, off, areas, areas_cap,
-                                           ctx->sm_count, s);
+            e = launch_areas_mode<kDirect>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
+                                 ctx->band_counts, ctx->sm_count, s);
             break;
         case SPHX_MODE_EFT_FP64:
-            e = launch_areas_mode<kEftFp64>(m, band_lo, band_hi, off, areas, areas_cap,
-                                            ctx->sm_count, s);
+            e = launch_areas_mode<kEftFp64>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
+                                 ctx->band_counts, ctx->sm_count, s);
             break;
         case SPHX_MODE_EFT_FF32:
-            e = launch_areas_mode<kEftFf32>(m, band_lo, band_hi, off, areas, areas_cap,
-                                            ctx->sm_count, s);
+            e = launch_areas_mode<kEftFf32>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
+                                 ctx->band_counts, ctx->sm_count, s);
             break;
         case SPHX_MODE_EFT_FP64_PRINTED:
-            e = launch_areas_mode<kEftFp64Printed>(m, band_lo, band_hi, off, areas, areas_cap,
-                                                   ctx->sm_count, s);
+            e = launch_areas_mode<kEftFp64Printed>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
+                                 ctx->band_counts, ctx->sm_count, s);
             break;
         case SPHX_MODE_WIDE_INT:
-            e = launch_areas_mode<kWideInt>(m, band_lo, band_hi, off, areas, areas_cap,
-                                            ctx->sm_count, s);
+            e = launch_areas_mode<kWideInt>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
+                                 ctx->band_counts, ctx->sm_count, s);
             break;
         default:
             return SPHX_ERR_INVALID_ARG;

@@ -109,13 +109,24 @@ sphx_status sphx::ensure_band_scratch(sphx_context *ctx, int64_t faces) {
     if (ctx->band_block_sums && ctx->band_faces >= faces) return SPHX_OK;
     SPHX_CUDA(cudaDeviceSynchronize());  // nothing may still use the old buffer
     cudaFree(ctx->band_block_sums);
+    cudaFree(ctx->band_lists);
+    cudaFree(ctx->band_counts);
     ctx->band_block_sums = nullptr;
+    ctx->band_lists = nullptr;
+    ctx->band_counts = nullptr;
     ctx->band_faces = 0;
     const int64_t cap = faces + faces / 4 + 1024;
     if (cudaMalloc(&ctx->band_block_sums, (scan_blocks_for(cap) + 1) * sizeof(long long)) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaMalloc(&ctx->band_lists, 2 * cap * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->band_counts, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(ctx->band_block_sums);
+        cudaFree(ctx->band_lists);
+        cudaFree(ctx->band_counts);
         ctx->band_block_sums = nullptr;
+        ctx->band_lists = nullptr;
+        ctx->band_counts = nullptr;
         return SPHX_ERR_NOMEM;
     }
     ctx->band_faces = cap;
@@ -415,6 +426,8 @@ void sphx_destroy(sphx_context *ctx) {
     free_scratch(ctx->scratch);
     free_host_staging(ctx->host);
     cudaFree(ctx->band_block_sums);
+    cudaFree(ctx->band_lists);
+    cudaFree(ctx->band_counts);
     cudaFree(ctx->zonal_acc);
     cudaFree(ctx->status);
     cudaStreamDestroy(ctx->capture_stream);
