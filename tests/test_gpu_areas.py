@@ -308,3 +308,16 @@ def test_one_call_zonal_sums(ctx):
     assert ctx.sync_status() == sphx.OK
     assert torch.equal(fa, fa2) and torch.equal(aa, aa2)
     np.testing.assert_allclose(aa.cpu().numpy(), TWO_PI * np.diff(lat), rtol=0, atol=1e-14)
+
+
+def test_big_cells_in_one_band(ctx):
+    """Cells of up to ~70 degrees radius inside one wide band: the one-band list
+    takes them, but with nodes more than 60 degrees from node 0 the triangle
+    fan passes them on to the boundary integral; cells that stick out of the
+    band stay with the boundary integral from the start."""
+    nodes, off, fn = W.polygon_cells(60, seed=35, radius=(0.3, 1.2), star=0.1)
+    cells = W.cells_as_lists(nodes, off, fn)
+    lat = np.array([-1.0, -0.999, 0.999, 1.0])
+    check_against_oracle(ctx, cells, lat)
+    lat = np.array([-1.0, -0.95, -0.3, 0.2, 0.97, 1.0])
+    check_against_oracle(ctx, cells, lat)
