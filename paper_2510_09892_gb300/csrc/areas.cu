@@ -35,10 +35,12 @@
 //                        the slot-1 hits of descending ones, an arc that
 //                        passes its highest (lowest) point being split there
 //                        into a rising and a falling run.
-//     Cells that lie inside one band (most, when cells are smaller than
-//     bands) take a shorter path: band_partition_kernel sorts the cells into
-//     two lists, and fan_area_kernel gives each one-band cell its own area,
-//     a fan of spherical triangles (Van Oosterom and Strackee's excess).
+//     Most cells take shorter paths: band_partition_kernel sorts the cells
+//     into three lists; fan_area_kernel gives each cell inside one band its
+//     own area, a fan of spherical triangles (Van Oosterom and Strackee's
+//     excess), and pair_area_kernel splits a cell cut by one latitude into
+//     the fan above the crossings plus the sliver under the latitude arc,
+//     and the rest.
 //  3. zonal_sum_kernel   per band, sum of field * area and of area, in 128-bit
 //                        fixed point with 64-bit integer atomics (per block in
 //                        shared memory, then once per block in global memory),
@@ -396,10 +398,11 @@ __device__ __forceinline__ void green_cell(const Mesh &m, int64_t f,
     }
 }
 
-// Cells are split in two lists (warp-aggregated appends, so warps stay
-// uniform): cells that lie inside one band other than the first and the last
-// (their widened height range is, so nothing was clamped), whose band area is
-// the cell's own area, and the others.
+// Cells are split in three lists (warp-aggregated appends, so warps stay
+// uniform): 0, cells that lie inside one band other than the first and the
+// last (their widened height range does, so nothing was clamped), whose band
+// area is the cell's own area; 2, cells in two such bands, cut by one
+// latitude; 1, the others.
 __global__ void band_partition_kernel(const int32_t *__restrict__ band_lo,
                                       const int32_t *__restrict__ band_hi, int64_t F, int64_t L,
                                       int32_t *__restrict__ lists, unsigned long long *counts) {
@@ -413,10 +416,11 @@ __global__ void band_partition_kernel(const int32_t *__restrict__ band_lo,
             nb = (int64_t)band_hi[f] - klo;
         }
         const bool one = f < F && nb == 1 && klo > 0 && klo < L - 2;
-        const bool other = f < F && nb > 0 && !one;
+        const bool two = f < F && nb == 2 && klo > 0 && klo + 1 < L - 2;
+        const bool other = f < F && nb > 0 && !one && !two;
 #pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            const bool mine = w == 0 ? one : other;
+        for (int w = 0; w < 3; ++w) {
+            const bool mine = w == 0 ? one : (w == 1 ? other : two);
             const unsigned bal = __ballot_sync(0xffffffffu, mine);
             if (!bal) continue;
             unsigned long long at = 0;
@@ -504,6 +508,187 @@ __global__ void __launch_bounds__(kAreaThreads, 8)
             if (lane == __ffs(bal) - 1) at = atomicAdd(counts + 1, (unsigned long long)__popc(bal));
             at = __shfl_sync(0xffffffffu, at, __ffs(bal) - 1);
             if (far) lists[m.n_faces + (int64_t)at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)f;
+        }
+    }
+}
+
+// fan area of the points p[0..n) (unit vectors) from p[0]; false when a point
+// is more than 60 degrees from p[0]
+__device__ __forceinline__ bool fan_of(const double (*p)[3], int n, double &area) {
+    area = 0.0;
+    for (int i = 1; i + 1 < n; ++i) {
+        const double *a = p[i], *b = p[i + 1], *o = p[0];
+        const double oa = fma(o[0], a[0], fma(o[1], a[1], o[2] * a[2]));
+        const double ob = fma(o[0], b[0], fma(o[1], b[1], o[2] * b[2]));
+        const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+        if (oa < 0.5 || ob < 0.5) return false;
+        const double d1x = a[0] - o[0], d1y = a[1] - o[1], d1z = a[2] - o[2];
+        const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
+        const double tri = fma(o[0], d1y * d2z - d1z * d2y,
+                               fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
+        const double t = tri / (1.0 + oa + ab + ob);
+        area += 2.0 * (fabs(t) <= 0.001953125 ? atan_small(t) : atan(t));
+    }
+    return true;
+}
+
+constexpr int kPairMaxNodes = 16;  // cells with more nodes take the boundary integral
+
+// A cell in two bands cut by the latitude z_j: with P_u and P_d its upward and
+// downward crossings of that latitude (Eq. 2.2 by the chosen mode; slot 0
+// crosses upwards along an arc, slot 1 downwards), the part above z_j is
+// bounded by the cell's boundary from P_u to P_d and by the latitude arc from
+// P_d eastward back to P_u (the interior lies to the left). Its area is the
+// fan of (P_u, the nodes between, P_d), closed by the great circle chord from
+// P_d to P_u, plus the sliver between that chord and the latitude arc,
+//   2 (atan(z tan(dl/2)) - z dl/2) = 2 (atan(z t) - z atan(t)),  t = tan(dl/2),
+// whose series for small t is 2 z (1 - z^2) t^3 (1/3 - (1 + z^2) t^2 / 5
+// + (1 + z^2 + z^4) t^4 / 7) (next term below 2^-54 of it for t <= 2^-9). The
+// part below is the cell's fan area minus that. Returns true, writing nothing,
+// for a cell this does not cover (not exactly one upward and one downward
+// crossing, more than kPairMaxNodes nodes, a point more than 60 degrees from
+// the first): it goes to the boundary integral.
+template <int Mode>
+__device__ __forceinline__ bool pair_area(const Mesh &m, int64_t f,
+                                          const int32_t *__restrict__ band_lo,
+                                          const long long *__restrict__ offsets,
+                                          double *__restrict__ areas, int64_t cap,
+                                          const double *lat) {
+    const long long off = offsets[f];
+    if (off < 0 || off + 2 > cap) {
+        atomicOr(m.status, kStatusCapacity);
+        return false;
+    }
+    int64_t s, e;
+    if (!cell_span(m, f, s, e)) return false;
+    const int nv = (int)(e - s);
+    if (nv < 3 || e - s > kPairMaxNodes) return true;
+    const double z = lat[band_lo[f] + 1];
+    double r[kPairMaxNodes][3];  // the nodes as given
+    double v[kPairMaxNodes][3];  // the nodes, unit length
+    for (int i = 0; i < nv; ++i) {
+        if (!node_at(m, s + i, r[i])) return false;
+        unit(r[i], v[i]);
+    }
+    // the arcs whose widened height range reaches z (only they can cross it);
+    // evaluated in a loop over this mask, so that a warp runs as many
+    // evaluations as its busiest lane needs, not one per arc
+    unsigned need = 0u;
+    for (int i = 0; i < nv; ++i) {
+        const int i1 = i + 1 < nv ? i + 1 : 0;
+        double zl, zh;
+        const bool ranged = z_range_fp32(r[i], r[i1], zl, zh) || z_range_fp64(r[i], r[i1], zl, zh);
+        if (!ranged || (zl <= z && z <= zh)) need |= 1u << i;
+    }
+    double Pu[3], Pd[3];
+    int au = -1, ad = -1, nu = 0, nd = 0;
+    bool up_first = false;
+    while (need) {
+        const int i = __ffs(need) - 1;
+        need &= need - 1u;
+        const int i1 = i + 1 < nv ? i + 1 : 0;
+        PairOut o;
+        intersect_pair<Mode>(r[i], r[i1], z, o);
+        if (o.count > 0) {
+            if (o.hit[0]) {
+                ++nu;
+                au = i;
+                Pu[0] = o.px[0];
+                Pu[1] = o.py[0];
+                Pu[2] = z;
+            }
+            if (o.hit[1]) {
+                ++nd;
+                ad = i;
+                Pd[0] = o.px[1];
+                Pd[1] = o.py[1];
+                Pd[2] = z;
+            }
+            // both on one arc: it rises first iff it passes its highest point
+            if (o.hit[0] && o.hit[1]) {
+                const double *a = r[i], *b = r[i1];
+                const double n0 = a[1] * b[2] - a[2] * b[1], n1 = a[2] * b[0] - a[0] * b[2];
+                up_first = n0 * a[1] - n1 * a[0] > 0.0;  // (n x a)_z > 0: rising at a
+            }
+        }
+    }
+    if (nu != 1 || nd != 1) return true;
+    // the cell's own fan area
+    double total;
+    if (!fan_of(v, nv, total)) return true;
+    // the part above z: P_u, the nodes after P_u's arc up to P_d's arc, P_d
+    double q[kPairMaxNodes + 2][3];
+    int nq = 0;
+    q[nq][0] = Pu[0];
+    q[nq][1] = Pu[1];
+    q[nq][2] = Pu[2];
+    ++nq;
+    int cnt = au == ad ? (up_first ? 0 : nv) : (ad - au + nv) % nv;
+    for (int k = 1; k <= cnt; ++k) {
+        const int i = (au + k) % nv;
+        q[nq][0] = v[i][0];
+        q[nq][1] = v[i][1];
+        q[nq][2] = v[i][2];
+        ++nq;
+    }
+    q[nq][0] = Pd[0];
+    q[nq][1] = Pd[1];
+    q[nq][2] = Pd[2];
+    ++nq;
+    double above;
+    if (!fan_of(q, nq, above)) return true;
+    // the sliver between the chord P_d -> P_u and the latitude arc
+    const double cr = Pd[0] * (Pu[1] - Pd[1]) - Pd[1] * (Pu[0] - Pd[0]);
+    const double rho2 = (1.0 - z) * (1.0 + z);
+    const double den = rho2 + fma(Pd[0], Pu[0], Pd[1] * Pu[1]);
+    if (!(cr > 0.0) || !(den > 0.0)) return true;  // P_u must lie east of P_d, within pi
+    const double t = cr / den;
+    double sliver;
+    if (t <= 0.001953125) {
+        const double z2 = z * z, t2 = t * t;
+        const double poly = fma(t2, fma(t2, fma(z2, z2, z2 + 1.0) / 7.0, -(1.0 + z2) / 5.0),
+                                1.0 / 3.0);
+        sliver = 2.0 * z * rho2 * (t * t2) * poly;
+    } else {
+        sliver = 2.0 * (atan(z * t) - z * atan(t));
+    }
+    above += sliver;
+    areas[off] = total - above;
+    areas[off + 1] = above;
+    return false;
+}
+
+// pair_area over the two-band list; a cell it does not cover is appended to
+// the other list (taken by band_area_kernel, launched after this kernel)
+template <int Mode>
+__global__ void __launch_bounds__(kAreaThreads)
+    pair_area_kernel(Mesh m, const int32_t *__restrict__ band_lo,
+                     const long long *__restrict__ offsets, double *__restrict__ areas, int64_t cap,
+                     int32_t *__restrict__ lists, unsigned long long *__restrict__ counts) {
+    extern __shared__ double s_lat[];
+    const double *lat = m.lat;
+    if (m.L <= kSmemLat) {
+        for (int64_t i = threadIdx.x; i < m.L; i += blockDim.x) s_lat[i] = m.lat[i];
+        __syncthreads();
+        lat = s_lat;
+    }
+    const int64_t n = (int64_t)counts[2];
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + lane;
+        bool back = false;
+        int64_t f = -1;
+        if (i < n) {
+            f = lists[2 * m.n_faces + i];
+            back = pair_area<Mode>(m, f, band_lo, offsets, areas, cap, lat);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, back);
+        if (bal) {
+            unsigned long long at = 0;
+            if (lane == __ffs(bal) - 1) at = atomicAdd(counts + 1, (unsigned long long)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, __ffs(bal) - 1);
+            if (back) lists[m.n_faces + (int64_t)at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)f;
         }
     }
 }
@@ -653,7 +838,7 @@ static cudaError_t launch_areas_mode(const Mesh &m, const int32_t *lo, const int
                                      const long long *off, double *areas, int64_t cap,
                                      int32_t *lists, unsigned long long *counts, int sm_count,
                                      cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int64_t need = (m.n_faces + 255) / 256;
     band_partition_kernel<<<(unsigned)std::min<int64_t>(need, (int64_t)sm_count * 8), 256, 0, s>>>(
@@ -665,6 +850,15 @@ static cudaError_t launch_areas_mode(const Mesh &m, const int32_t *lo, const int
     int64_t grid = std::min<int64_t>((m.n_faces + kAreaThreads - 1) / kAreaThreads,
                                      (int64_t)std::max(per_sm, 1) * sm_count);
     fan_area_kernel<<<(unsigned)grid, kAreaThreads, 0, s>>>(m, off, areas, cap, lists, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem1 = m.L <= kSmemLat ? (size_t)m.L * sizeof(double) : 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_area_kernel<Mode>, kAreaThreads,
+                                                      smem1);
+    if (e != cudaSuccess) return e;
+    grid = std::min<int64_t>((m.n_faces + kAreaThreads - 1) / kAreaThreads,
+                             (int64_t)std::max(per_sm, 1) * sm_count);
+    pair_area_kernel<Mode><<<(unsigned)grid, kAreaThreads, smem1, s>>>(m, lo, off, areas, cap, lists,
+                                                                        counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = m.L <= kSmemLat ? 2 * (size_t)m.L * sizeof(double) : 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_area_kernel<Mode>, kAreaThreads,

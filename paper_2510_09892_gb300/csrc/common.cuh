@@ -115,7 +115,7 @@ struct sphx_context {
     std::map<sphx::GraphKey, cudaGraphExec_t> graphs;
     sphx::HostStaging host;
     long long *band_block_sums = nullptr;  // band ranges' prefix sum: per scan block
-    int32_t *band_lists = nullptr;         // band areas: the two cell lists (2 x band_faces)
+    int32_t *band_lists = nullptr;         // band areas: the three cell lists (3 x band_faces)
     unsigned long long *band_counts = nullptr;  // their lengths
     int64_t band_faces = 0;                // cells these buffers serve
     unsigned long long *zonal_acc = nullptr;  // zonal sums: 4 words per band

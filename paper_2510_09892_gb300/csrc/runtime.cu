@@ -118,8 +118,8 @@ sphx_status sphx::ensure_band_scratch(sphx_context *ctx, int64_t faces) {
     const int64_t cap = faces + faces / 4 + 1024;
     if (cudaMalloc(&ctx->band_block_sums, (scan_blocks_for(cap) + 1) * sizeof(long long)) !=
             cudaSuccess ||
-        cudaMalloc(&ctx->band_lists, 2 * cap * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&ctx->band_counts, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->band_lists, 3 * cap * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->band_counts, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(ctx->band_block_sums);
         cudaFree(ctx->band_lists);
