@@ -321,3 +321,12 @@ def test_big_cells_in_one_band(ctx):
     check_against_oracle(ctx, cells, lat)
     lat = np.array([-1.0, -0.95, -0.3, 0.2, 0.97, 1.0])
     check_against_oracle(ctx, cells, lat)
+
+
+def test_cells_with_many_nodes(ctx):
+    """Polygons of 17-24 nodes: more than the two-band path keeps, so cells cut
+    by one latitude go to the boundary integral; one-band cells still take the
+    triangle fan."""
+    nodes, off, fn = W.polygon_cells(80, seed=36, radius=(2e-3, 0.05), kmin=17, kmax=24)
+    cells = W.cells_as_lists(nodes, off, fn)
+    check_against_oracle(ctx, cells, W.latlon_latitudes(361))
