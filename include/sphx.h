@@ -267,7 +267,13 @@ sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, int64_t n_n
    times (the sum over the cell's arcs of their longitude spans plus the
    cell's height range). Entries past
    areas_cap are not written (sphx_sync_status() reports SPHX_ERR_CAPACITY).
-   mode: any sphx_mode. Stream ordered; allocates nothing. */
+   Cells inside one band (other than the first and the last) get their own
+   area, a fan of spherical triangles (Van Oosterom and Strackee's excess);
+   cells cut by one latitude get the fan above their two crossings plus the
+   sliver under the latitude arc; the rest take the boundary integral. The
+   cell lists live in ctx's scratch (allocated when a call needs more, then
+   kept; calls on one context must not overlap in time). mode: any
+   sphx_mode. Stream ordered. */
 sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, int64_t n_nodes,
                             const int64_t *face_offsets, const int32_t *face_nodes,
                             int64_t n_face_nodes, int64_t n_faces, const double *lat_z,
