@@ -1,51 +1,48 @@
 // Band areas of spherical cells and zonal sums: the zonal-mean step that
 // Sec. 1 names as the use of arc-latitude intersections.
 //
-//  1. band_range_kernel  one thread per cell: the height range of its arcs
-//                        (ranges.cuh) and its winding number around the
-//                        z-axis give the bands [lo, hi) it can meet; the
-//                        ragged call's prefix sum turns the counts into
-//                        output offsets.
-//  2. band_area_kernel   one thread per cell. In longitude and height the
-//                        area element is dlambda dz, so by Green's theorem a
-//                        region's area is the boundary integral of lambda dz.
-//                        The boundary of (cell ∩ band) consists of arc pieces
-//                        and latitude pieces; the latter have dz = 0. So each
-//                        arc is cut at its crossings with the latitudes
-//                        (Eq. 2.2, evaluated by the chosen mode), and every
-//                        piece p -> q adds
-//                            lambda_q z_q - lambda_p z_p - T(p, q)
-//                        to the band it lies in, where T(p, q), the integral
-//                        of z dlambda along the piece, is the signed area
-//                        between the piece and the equator:
-//                            T = 2 atan2(sin(dl/2) (t_p + t_q),
-//                                        cos(dl/2) (1 + t_p t_q)),
-//                        t = tan(latitude / 2) = z / (1 + rho), with the
-//                        half-angle ratio tan(dl/2) = cr / (rho_p rho_q + dt)
-//                        from the pieces' xy cross and dot products.
-//                        lambda is unwrapped along the cell from its first
-//                        node off the poles (lambda = 0 there); a cell around
-//                        a pole (winding +-1) needs a cut from that node to
-//                        the pole, across which lambda jumps by 2 pi: it adds
-//                        2 pi times each band's share of the cut's height.
-//                        Crossings come in order along the arc without a
-//                        sort: slot 0 of Eq. 2.2 crosses upwards along the
-//                        arc and slot 1 downwards, so a rising run takes the
-//                        slot-0 hits of ascending latitudes and a falling run
-//                        the slot-1 hits of descending ones, an arc that
-//                        passes its highest (lowest) point being split there
-//                        into a rising and a falling run.
-//     Most cells take shorter paths: band_partition_kernel sorts the cells
-//     into three lists; fan_area_kernel gives each cell inside one band its
-//     own area, a fan of spherical triangles (Van Oosterom and Strackee's
-//     excess), and pair_area_kernel splits a cell cut by one latitude into
-//     the fan above the crossings plus the sliver under the latitude arc,
-//     and the rest.
-//  3. zonal_sum_kernel   per band, sum of field * area and of area, in 128-bit
-//                        fixed point with 64-bit integer atomics (per block in
-//                        shared memory, then once per block in global memory),
-//                        so the result does not depend on the order of the
-//                        additions.
+//  1. band_range_kernel   one thread per cell: the height range of its arcs
+//                         (ranges.cuh) and its winding number around the
+//                         z-axis give the bands [lo, hi) it can meet; the
+//                         ragged call's prefix sum turns the counts into
+//                         output offsets.
+//  2. band_partition_kernel sorts the cells into three lists, so that every
+//     kernel below sees uniform warps:
+//     fan_area_kernel     cells inside one band: the band area is the cell's
+//                         own area, a fan of spherical triangles (Van
+//                         Oosterom and Strackee's excess).
+//     pair_area_kernel    cells cut by one latitude: the fan above its two
+//                         crossings (Eq. 2.2) plus the sliver between the
+//                         closing chord and the latitude arc; the part below
+//                         is the cell's fan minus that.
+//     band_area_kernel    every other cell, by the boundary integral. In
+//                         longitude and height the area element is
+//                         dlambda dz, so by Green's theorem a region's area is
+//                         the boundary integral of lambda dz; the latitude
+//                         pieces of the boundary of (cell ∩ band) have dz = 0.
+//                         Each arc is cut at its crossings with the latitudes
+//                         (Eq. 2.2 by the chosen mode), and each piece p -> q
+//                         adds lambda_p (z_q - z_p) + dl z_q - T to the band
+//                         holding its midpoint: dl is its longitude step and
+//                         T = 2 atan(K h) the signed area between it and the
+//                         equator, with h = tan(dl / 2) from the xy cross and
+//                         dot products and K = (t_p + t_q) / (1 + t_p t_q),
+//                         t = tan(latitude / 2). lambda is unwrapped along the
+//                         cell from its first node off the poles; a cell
+//                         around a pole adds 2 pi times each band's share of
+//                         the height from that node to the pole (the cut
+//                         across which lambda jumps by 2 pi). Crossings come
+//                         in order along the arc without a sort: slot 0 of
+//                         Eq. 2.2 crosses upwards along the arc and slot 1
+//                         downwards, so a rising run takes the slot-0 hits of
+//                         ascending latitudes and a falling run the slot-1
+//                         hits of descending ones (an arc that passes its
+//                         highest or lowest point is split there).
+//  3. zonal_sum_kernel    per band, sum of field * area and of area, in
+//                         128-bit fixed point with 64-bit integer atomics (per
+//                         block in shared memory, then once per block in
+//                         global memory), so the result does not depend on the
+//                         order of the additions.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
