@@ -601,11 +601,15 @@ __device__ __forceinline__ bool pair_area(const Mesh &m, int64_t f,
                 Pd[1] = o.py[1];
                 Pd[2] = z;
             }
-            // both on one arc: it rises first iff it passes its highest point
+            // both on one arc: the one nearer the arc's start comes first
+            // (distance from the start grows along a minor arc)
             if (o.hit[0] && o.hit[1]) {
-                const double *a = r[i], *b = r[i1];
-                const double n0 = a[1] * b[2] - a[2] * b[1], n1 = a[2] * b[0] - a[0] * b[2];
-                up_first = n0 * a[1] - n1 * a[0] > 0.0;  // (n x a)_z > 0: rising at a
+                const double *u = v[i];
+                const double du = (Pu[0] - u[0]) * (Pu[0] - u[0]) + (Pu[1] - u[1]) * (Pu[1] - u[1]) +
+                                  (z - u[2]) * (z - u[2]);
+                const double dd = (Pd[0] - u[0]) * (Pd[0] - u[0]) + (Pd[1] - u[1]) * (Pd[1] - u[1]) +
+                                  (z - u[2]) * (z - u[2]);
+                up_first = du < dd;
             }
         }
     }

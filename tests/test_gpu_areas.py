@@ -330,3 +330,19 @@ def test_cells_with_many_nodes(ctx):
     nodes, off, fn = W.polygon_cells(80, seed=36, radius=(2e-3, 0.05), kmin=17, kmax=24)
     cells = W.cells_as_lists(nodes, off, fn)
     check_against_oracle(ctx, cells, W.latlon_latitudes(361))
+
+
+def test_both_crossings_on_one_arc(ctx):
+    """A latitude just above a quadrilateral's top corners: the top arc (a great
+    circle between two points at one latitude) bulges poleward across it and
+    back, so one arc holds both crossings (rising first); the mirror image in
+    the south has them on its bottom arc, falling first."""
+    north = [_sph(20, 30), _sph(50, 30), _sph(50, 31), _sph(20, 31)]
+    south = [(x, y, -z) for (x, y, z) in reversed(north)]
+    zt = math.sin(math.radians(31))
+    apex = max(OA.breakpoints([_sph(50, 31), _sph(20, 31)]))
+    assert apex > zt
+    zj = 0.5 * (zt + apex)
+    lat = [-1.0, 0.3, 0.49, zj, apex + 0.01, 0.9, 1.0]
+    check_against_oracle(ctx, [north], lat)
+    check_against_oracle(ctx, [south], [-z for z in reversed(lat)])
