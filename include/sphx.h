@@ -227,7 +227,8 @@ sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const doub
                    nonzero length;
      face_offsets  device int64[n_faces + 1]: cell f is the node list
                    face_nodes[face_offsets[f] .. face_offsets[f + 1]);
-     face_nodes    device int32[n_face_nodes]: node indices.
+     face_nodes    device int32[n_face_nodes]: node indices
+                   (n_nodes and n_faces below 2^31).
    A cell is a simple spherical polygon whose consecutive nodes (and the last
    and the first) are joined by minor great circle arcs, counter-clockwise
    seen from outside the sphere, with at most one pole in its interior (a pole

@@ -881,9 +881,10 @@ namespace {
 bool valid_mesh(sphx_context *ctx, const double *nodes, int64_t n_nodes,
                 const int64_t *face_offsets, const int32_t *face_nodes, int64_t n_face_nodes,
                 int64_t n_faces, const double *lat_z, int64_t n_lat) {
-    return ctx && n_faces >= 0 && n_nodes >= 0 && n_face_nodes >= 0 && n_lat >= 2 &&
-           n_lat <= INT32_MAX && (n_faces == 0 || (nodes && face_offsets && face_nodes)) &&
-           lat_z;
+    // cells and nodes are indexed by int32 (node indices, the cell lists)
+    return ctx && n_faces >= 0 && n_faces <= INT32_MAX && n_nodes >= 0 && n_nodes <= INT32_MAX &&
+           n_face_nodes >= 0 && n_lat >= 2 && n_lat <= INT32_MAX &&
+           (n_faces == 0 || (nodes && face_offsets && face_nodes)) && lat_z;
 }
 
 Mesh make_mesh(sphx_context *ctx, const double *nodes, int64_t n_nodes,

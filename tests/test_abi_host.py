@@ -77,6 +77,7 @@ def test_band_area_argument_errors_before_launch():
     assert r(ctx, FAKE, 10, FAKE, FAKE, 40, -1, FAKE, 5, FAKE, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
     assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, None, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
     assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, None, None) == sphx.ERR_INVALID_ARG
+    assert r(ctx, FAKE, 10, FAKE, FAKE, 40, 1 << 31, FAKE, 5, FAKE, FAKE, FAKE, None) == sphx.ERR_INVALID_ARG
     a = L.sphx_band_areas
     assert a(ctx, FAKE, 10, FAKE, FAKE, 40, 10, FAKE, 5, FAKE, FAKE, FAKE, 4, FAKE, -1,
              None) == sphx.ERR_INVALID_ARG
