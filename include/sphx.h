@@ -151,7 +151,7 @@ sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A,
 sphx_status sphx_host_join(sphx_context *ctx, sphx_stream stream);
 
 /* Intersection of two great circle arcs, pair i = (A1[i], A2[i]) and
-   (B1[i], B2[i]): the "three cross products and a normalisation" of Sec. 1
+   (B1[i], B2[i]): three cross products followed by a normalisation (Sec. 1)
    (Sec. 9 names it as a use of the accurate cross product). The circles meet
    at +-v / |v|, v = (a1 x a2) x (b1 x b2); a point is a hit iff it lies on
    both closed minor arcs, decided as in the latitude call. A1, A2, B1, B2:

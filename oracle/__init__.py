@@ -21,8 +21,8 @@ Contents
                ``fma``/``sqrt``, built with ``-ffp-contract=off``.
 ``ragged``     Brute force over every (edge, latitude) pair of a mesh batch,
                using ``exact``.
-``exact_arcs`` Intersection of two great circle arcs (the "three cross products
-               and a normalisation" of Sec. 1): v = n_a x n_b exactly, the
+``exact_arcs`` Intersection of two great circle arcs (three cross products
+               followed by a normalisation, Sec. 1): v = n_a x n_b exactly, the
                on-arc signs exactly, v / |v| correctly rounded.
 
 Pinning

@@ -8,8 +8,8 @@ What it computes (the plain definition)
 Two arcs a = (a1, a2) and b = (b1, b2), each the shorter great circle arc
 between two FP64 points taken as exact reals (Sec. 1.2). Their great circles
 have the normals n_a = a1 x a2 and n_b = b1 x b2 and meet in the two
-antipodal points +-v / |v|, v = n_a x n_b: the "three cross products and a
-normalisation" of Sec. 1. A candidate p is a hit iff it lies on both closed
+antipodal points +-v / |v|, v = n_a x n_b: three cross products followed by a
+normalisation (Sec. 1). A candidate p is a hit iff it lies on both closed
 minor arcs, which we decide as for the latitude problem: (a1 x p) . n_a >= 0
 and (p x a2) . n_a >= 0, and the same for b. Slot 0 holds +v / |v|, slot 1
 -v / |v|; each coordinate of a hit is the exact value v_i / |v| correctly

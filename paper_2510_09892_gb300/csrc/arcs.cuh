@@ -1,5 +1,5 @@
 // Per-pair intersection of two great circle arcs a = (a1, a2), b = (b1, b2):
-// "three cross products and a normalisation" (Sec. 1 of arXiv 2510.09892;
+// three cross products followed by a normalisation (Sec. 1 of arXiv 2510.09892;
 // Sec. 9 names it as a use of the accurate cross product). The great circles
 // meet at +-v / |v|, v = n_a x n_b with n_a = a1 x a2, n_b = b1 x b2; slot 0
 // holds +v / |v|, slot 1 -v / |v|; a slot is a hit iff the point lies on both
