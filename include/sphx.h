@@ -209,7 +209,13 @@ sphx_status sphx_candidate_ranges(const double *A, const double *B, const int64_
    record. Scratch comes from the context (allocated on the first call for a
    given size, then reused); the launch sequence is captured in a CUDA graph
    on the first call with a given argument set and replayed afterwards.
-   Calls on one context must not overlap in time. */
+   Calls on one context must not overlap in time. The ordered compaction's
+   look-back waits at most about 2e6 sleeps of 64 ns per chunk; one that runs
+   out records SPHX_ERR_TIMEOUT (the records are then incomplete) and the
+   call still ends. Failure injection for tests, read from the environment on
+   each call: SPHX_FAULT=alloc makes a scratch allocation fail (ERR_NOMEM),
+   SPHX_FAULT=lookback makes the first chunk withhold its prefix so that the
+   look-back runs out (ERR_TIMEOUT from sphx_sync_status). */
 sphx_status sphx_intersect_ragged(sphx_context *ctx, const double *A, const double *B,
                                   const int64_t *edge_offsets, int32_t M, int64_t E,
                                   const double *lat_z, const int64_t *lat_offsets, int64_t L,

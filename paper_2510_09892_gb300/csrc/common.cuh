@@ -68,6 +68,8 @@ struct RaggedArgs {
     unsigned long long *ring;      // look-back ring (ORDERED)
     int64_t ring_slots;            // power of two
     unsigned *status;
+    int hold_first;                // failure injection (tests): chunk 0 never publishes its
+                                   // prefix, so the look-back of chunk 1 waits out its limit
 };
 
 // ragged.cu

@@ -272,7 +272,7 @@ __global__ void ragged_kernel(RaggedArgs a) {
                 const unsigned long long mask = (unsigned long long)a.ring_slots - 1;
                 const unsigned long long tag = c >> ring_bits;
                 if (c == 0) {
-                    atomicExch(a.ring, lb_pack(kFlagInc, 0, total));
+                    if (!a.hold_first) atomicExch(a.ring, lb_pack(kFlagInc, 0, total));
                 } else {
                     atomicExch(a.ring + (c & mask), lb_pack(kFlagAgg, tag, total));
                     unsigned long long run = 0;

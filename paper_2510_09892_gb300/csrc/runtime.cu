@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace sphx {
@@ -98,6 +100,22 @@ bool mapped_host(const void *p, size_t bytes) {
     return true;
 }
 
+// a named range in the profiler's timeline for as long as the scope lasts
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// host-side failure injection for the tests: SPHX_FAULT=alloc makes scratch
+// allocation fail, SPHX_FAULT=lookback makes the ordered compaction's first
+// chunk withhold its prefix (the bounded look-back then reports a timeout)
+bool fault_is(const char *what) {
+    const char *f = std::getenv("SPHX_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
 void drop_graphs(sphx_context *ctx) {
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
@@ -159,7 +177,7 @@ sphx_status ensure_scratch(sphx_context *ctx, int64_t E) {
     free_scratch(s);
     const int64_t cap = E + E / 4 + 1024;  // headroom so slightly larger batches reuse it
     const int64_t nb = scan_blocks_for(cap);
-    if (std::getenv("SPHX_FAULT") && std::strcmp(std::getenv("SPHX_FAULT"), "alloc") == 0)
+    if (fault_is("alloc"))
         return SPHX_ERR_NOMEM;
     bool ok = cudaMalloc(&s.lo, cap * sizeof(int32_t)) == cudaSuccess &&
               cudaMalloc(&s.hi, cap * sizeof(int32_t)) == cudaSuccess &&
@@ -229,6 +247,7 @@ cudaError_t enqueue_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedS
     a.ring = sc.ring;
     a.ring_slots = slots;
     a.status = ctx->status;
+    a.hold_first = fault_is("lookback") ? 1 : 0;
     return launch_ragged(c.mode, sh, a, ctx->sm_count, s);
 }
 
@@ -268,9 +287,10 @@ sphx_status run_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedShape
              (uintptr_t)c.lo, (uintptr_t)c.hi, (uintptr_t)c.mode, (uintptr_t)c.out,
              (uintptr_t)c.cap, (uintptr_t)c.out_total, (uintptr_t)sh.threads,
              (uintptr_t)sh.blocks_per_sm, (uintptr_t)sh.pairs_per_lane,
-             (uintptr_t)sh.compaction};
+             (uintptr_t)sh.compaction, (uintptr_t)fault_is("lookback")};
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
+        NvtxRange r("sphx ragged: capture");
         if (ctx->graphs.size() >= 64) drop_graphs(ctx);
         cudaGraph_t g = nullptr;
         SPHX_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -288,6 +308,7 @@ sphx_status run_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedShape
         SPHX_CUDA(e);
         it = ctx->graphs.emplace(key, ex).first;
     }
+    NvtxRange r("sphx ragged: replay");
     SPHX_CUDA(cudaGraphLaunch(it->second, s));
     return SPHX_OK;
 }

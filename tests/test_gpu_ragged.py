@@ -269,3 +269,45 @@ def test_full_size_cubed_sphere_sampled(ctx):
     z0 = batch["lat_z"][recs["lat"]]
     r2 = recs["x"] ** 2 + recs["y"] ** 2 + z0 ** 2
     assert np.abs(r2 - 1).max() < 1e-14
+
+
+def test_injected_lookback_stall_times_out_and_context_recovers(monkeypatch):
+    """Failure injection on the host side: with SPHX_FAULT=lookback the first
+    chunk of the ordered compaction never publishes its prefix, so the next
+    chunk's look-back waits on a flag that nothing sets. The wait is bounded:
+    the call ends, sync_status reports ERR_TIMEOUT, and the same context then
+    gives the exact records once the fault is lifted."""
+    batch = W.ragged_meshes(2, 40, 80, seed=12, lat_min=180, lat_max=260)
+    d = to_dev(batch)
+    key, x, y = all_pairs_reference(batch)
+    assert len(key) > 64  # more than one chunk of 32 pairs
+    with sphx.Context(0) as c:
+        c.set_tuning(compaction=sphx.COMPACT_ORDERED, use_graph=0)
+        monkeypatch.setenv("SPHX_FAULT", "lookback")
+        st, _, _ = run_ragged(c, d, "eft")
+        assert st == sphx.ERR_TIMEOUT
+        monkeypatch.delenv("SPHX_FAULT")
+        assert c.sync_status() == sphx.OK  # the status word was cleared
+        st, total, recs = run_ragged(c, d, "eft")
+        assert st == sphx.OK and total == len(key)
+        got = np.stack([recs["edge"], recs["lat"].astype(np.int64),
+                        recs["root"].astype(np.int64)], 1)
+        assert np.array_equal(got, key) and P.same_bits(recs["x"], x)
+
+
+def test_injected_scratch_allocation_failure(monkeypatch):
+    """SPHX_FAULT=alloc makes the scratch allocation of a fresh context fail:
+    the call returns ERR_NOMEM before any launch, and the context works once
+    the fault is lifted."""
+    batch = small_batch(seed=13)
+    d = to_dev(batch)
+    with sphx.Context(0) as c:
+        monkeypatch.setenv("SPHX_FAULT", "alloc")
+        with pytest.raises(sphx.SphxError) as ei:
+            run_ragged(c, d, "eft")
+        assert ei.value.status == sphx.ERR_NOMEM
+        monkeypatch.delenv("SPHX_FAULT")
+        st, total, recs = run_ragged(c, d, "eft")
+        key, x, y = all_pairs_reference(batch)
+        got, gx, gy = sorted_records(recs)
+        assert st == sphx.OK and np.array_equal(got, key) and P.same_bits(gx, x)
