@@ -56,8 +56,10 @@ TRAFFIC_PER_LAUNCH = {"wide": 56.056e6 + 8.937e6}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
-          "direct": "f64", "ff32": "f32 pairs + f64"}
+          "direct": "f64", "ff32": "f32 pairs + f64",
+          "adaptive": "f64 with a running error bound, u32 limbs where it fails"}
 L2_FLUSH_BYTES = 256 << 20
+ADAPTIVE_GATES = (4.0, 64.0, 2.0 ** 20)  # ulp per component; 4 is the adaptive mode's own
 CPU_SAMPLE = 32_768            # arcs per oracle step
 
 
@@ -317,6 +319,7 @@ def main():
     clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
 
     arcs = arcs_leg(sphx, torch, dev, args, flush) if rank == 0 else None
+    adaptive = adaptive_leg(sphx, torch, dev, args, flush, (A, B, z)) if rank == 0 else None
     ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
     zonal = zonal_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
     meshes = (meshes_leg(sphx, torch, dev, args, head, mesh_pool)
@@ -379,6 +382,8 @@ def main():
         line["cpu_baseline"] = cpu
     if arcs is not None:
         line["arc_x_arc"] = arcs
+    if adaptive is not None:
+        line["adaptive_filter"] = adaptive
     if ragged is not None:
         line["ragged_regridding"] = ragged
     if zonal is not None:
@@ -419,6 +424,50 @@ def arcs_leg(sphx, torch, dev, args, flush) -> dict:
         res["modes"][mode] = {"ms_per_step": m, "pairs_per_s": n / (m * 1e-3),
                               "hbm_frac": 148 * n / (m * 1e-3) / 1e9 / measured_hbm_peak()}
     res["hits"] = int(torch.clamp(cnt, min=0).sum().item())
+    return res
+
+
+def adaptive_leg(sphx, torch, dev, args, flush, stress) -> dict:
+    """The adaptive filter (not the headline): on the 10^6 stress arcs and on
+    10^6 well-conditioned arcs (uniform endpoints, arc length uniform in
+    (0, pi/2), one latitude inside each arc's z-range), the time per dense call
+    of the adaptive mode beside the integer-limb and direct FP64 forms, and the
+    share of arcs the filter hands on to the integer-limb form."""
+    cur = torch.cuda.current_stream(dev)
+    res = {"workloads": {}}
+    for name in ("stress", "uniform"):
+        A, B, z = stress if name == "stress" else W.uniform_arcs(N_ARCS, seed=W.DEFAULT_SEED + 5)
+        tA, tB, tz = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (A, B, z))
+        n = len(z)
+        pts = torch.empty((n, 2, 3), dtype=torch.float64, device=dev)
+        cnt = torch.empty(n, dtype=torch.int32, device=dev)
+        entry = {"arcs": n, "fallback_share": {}, "ms_per_step": {}}
+        fb = torch.zeros(1, dtype=torch.int64, device=dev)
+        calls = {"wide": lambda: sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "wide", cur),
+                 "direct": lambda: sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "direct",
+                                                                    cur)}
+        for gate in ADAPTIVE_GATES:
+            fb.zero_()
+            sphx.sphx_intersect_gca_constlat_adaptive(tA, tB, tz, pts, cnt, gate, fb, cur)
+            torch.cuda.synchronize()
+            entry["fallback_share"][f"{gate:g} ulp"] = int(fb.item()) / n
+            calls[f"adaptive, {gate:g} ulp"] = (
+                lambda g=gate: sphx.sphx_intersect_gca_constlat_adaptive(tA, tB, tz, pts, cnt, g,
+                                                                         None, cur))
+        for key, call in calls.items():
+            ms = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(cur)
+                call()
+                e1.record(cur)
+                if i >= args.warmup:
+                    ms.append((e0, e1))
+            torch.cuda.synchronize()
+            entry["ms_per_step"][key] = statistics.mean(a.elapsed_time(b) for a, b in ms)
+        res["workloads"][name] = entry
     return res
 
 

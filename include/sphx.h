@@ -77,7 +77,18 @@ typedef enum {
        SPHX_MODE_EFT_FP64 (<= 4 ulp per component of the correctly rounded
        exact point), computed on the integer pipe, which GB300 runs 32 times
        faster than its FP64 pipe. */
-    SPHX_MODE_WIDE_INT = 4
+    SPHX_MODE_WIDE_INT = 4,
+    /* The adaptive filter (Sec. 9): Eq. 2.2 in plain FP64 (FMA cross
+       products, one correctly rounded sqrt and division per coordinate) with
+       a running forward error bound. A lane is kept when the bound proves its
+       hit count (sign of s^2, both on-arc signs) and every point component
+       within the 4-ulp gate (4 ulp of the correctly rounded value where
+       |P_c| >= 2^-20 sqrt(1 - z0^2), 4 u sqrt(1 - z0^2) absolute below);
+       otherwise the lane is re-evaluated as in SPHX_MODE_WIDE_INT (tangency,
+       near-endpoint and degenerate arcs, inputs outside [2^-100, 2^100]).
+       Every result therefore meets the SPHX_MODE_EFT_FP64 bound. Dense and
+       host-buffer calls only (the others return SPHX_ERR_UNSUPPORTED). */
+    SPHX_MODE_ADAPTIVE = 5
 } sphx_mode;
 
 /* Output compaction scheme of the ragged call. */
@@ -123,6 +134,21 @@ void sphx_destroy(sphx_context *ctx);
 sphx_status sphx_intersect_gca_constlat(const double *A, const double *B, const double *z0,
                                         int64_t n, double *out_pts, int32_t *out_count,
                                         sphx_mode mode, sphx_stream stream);
+
+/* The adaptive mode with a caller's gate and its statistics: as
+   sphx_intersect_gca_constlat with mode SPHX_MODE_ADAPTIVE, except that the
+   filter keeps a lane when its bound proves each point component within
+   gate_ulps ulp (gate_ulps u sqrt(1 - z0^2) for components below
+   2^-20 sqrt(1 - z0^2)); 4 is the mode's own gate. gate_ulps in [1, 2^26],
+   else SPHX_ERR_INVALID_ARG. Re-evaluated lanes are correctly rounded from
+   96 bits whatever the gate. Atomically adds to *fallback_count (device
+   uint64, 8-byte aligned, may be NULL) the number of arcs the filter handed
+   to the integer-limb form. Stream ordered; allocates nothing. */
+sphx_status sphx_intersect_gca_constlat_adaptive(const double *A, const double *B,
+                                                 const double *z0, int64_t n, double *out_pts,
+                                                 int32_t *out_count, double gate_ulps,
+                                                 unsigned long long *fallback_count,
+                                                 sphx_stream stream);
 
 /* Dense call on HOST buffers (same problem and layouts as
    sphx_intersect_gca_constlat; A, B, z0, out_pts, out_count are host

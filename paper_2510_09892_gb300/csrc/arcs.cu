@@ -114,7 +114,8 @@ extern "C" sphx_status sphx_intersect_gca_gca(const double *A1, const double *A2
         case SPHX_MODE_EFT_FP64: launch_arcs<kEftFp64>(A1, A2, B1, B2, n, out_pts, out_count, s); break;
         case SPHX_MODE_WIDE_INT: launch_arcs<kWideInt>(A1, A2, B1, B2, n, out_pts, out_count, s); break;
         case SPHX_MODE_EFT_FF32:
-        case SPHX_MODE_EFT_FP64_PRINTED: return SPHX_ERR_UNSUPPORTED;
+        case SPHX_MODE_EFT_FP64_PRINTED:
+        case SPHX_MODE_ADAPTIVE: return SPHX_ERR_UNSUPPORTED;
         default: return SPHX_ERR_INVALID_ARG;
     }
     cudaError_t e = cudaGetLastError();

@@ -977,6 +977,8 @@ extern "C" sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, i
             e = launch_areas_mode<kWideInt>(m, band_lo, band_hi, off, areas, areas_cap, ctx->band_lists,
                                  ctx->band_counts, ctx->sm_count, s);
             break;
+        case SPHX_MODE_ADAPTIVE:
+            return SPHX_ERR_UNSUPPORTED;
         default:
             return SPHX_ERR_INVALID_ARG;
     }

@@ -1,0 +1,175 @@
+// Dense call: one latitude per arc (sphx_intersect_gca_constlat).
+//
+// One thread evaluates one arc (both roots). A block owns a tile of kTile
+// consecutive arcs: the tile's endpoints (kTile x 3 doubles each, contiguous
+// in the caller's row-major (n, 3) arrays) and latitudes are staged into
+// shared memory with coalesced 16-byte loads, the per-thread work runs from
+// registers, and the tile's results (kTile x 6 doubles, kTile counts) are
+// staged back through shared memory and written with coalesced 16-byte
+// stores. The grid is one wave of resident blocks (a multiple of the SM count)
+// and strides over the tiles.
+//
+// The adaptive mode runs in two phases per tile: every thread first tries the
+// filtered FP64 evaluation; the lanes it cannot vouch for append their tile
+// index to a shared-memory queue (one atomic per warp), and after a barrier
+// the block's first threads evaluate the queued arcs with the integer-limb
+// form, densely, so that the accurate form's divergence is confined to the
+// queue's last warp instead of every warp that holds one failing lane.
+#pragma once
+#include <algorithm>
+
+#include "adaptive.cuh"
+#include "common.cuh"
+#include "intersect.cuh"
+
+namespace sphx {
+
+constexpr int kTile = 128;  // arcs per tile = threads per block
+constexpr int kAdaptive = 5;
+
+template <int Mode>
+__global__ void __launch_bounds__(kTile) dense_kernel(const double *__restrict__ A,
+                                                      const double *__restrict__ B,
+                                                      const double *__restrict__ Z, int64_t n,
+                                                      double *__restrict__ out_pts,
+                                                      int32_t *__restrict__ out_count,
+                                                      unsigned long long *fallback,
+                                                      double gate) {
+    __shared__ __align__(16) double sA[3 * kTile];
+    __shared__ __align__(16) double sB[3 * kTile];
+    __shared__ __align__(16) double sZ[kTile];
+    __shared__ __align__(16) double sP[6 * kTile];
+    __shared__ __align__(16) int32_t sC[kTile];
+    __shared__ int sQ[Mode == kAdaptive ? kTile : 1];
+    __shared__ int sQn;
+    const int t = threadIdx.x;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    auto stage_result = [&](int j, const PairOut &o, double z0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            sP[6 * j + 3 * r + 0] = o.hit[r] ? o.px[r] : nan;
+            sP[6 * j + 3 * r + 1] = o.hit[r] ? o.py[r] : nan;
+            sP[6 * j + 3 * r + 2] = o.hit[r] ? z0 : nan;
+        }
+        sC[j] = o.count;
+    };
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * kTile;
+        const int cnt = (int)(n - base < kTile ? n - base : kTile);
+        if (Mode == kAdaptive && t == 0) sQn = 0;
+        if (cnt == kTile) {
+            // full tile: 16-byte loads (base is a multiple of kTile, so
+            // 3 * base doubles is a multiple of 16 bytes)
+            const double2 *A2 = reinterpret_cast<const double2 *>(A + 3 * base);
+            const double2 *B2 = reinterpret_cast<const double2 *>(B + 3 * base);
+            const double2 *Z2 = reinterpret_cast<const double2 *>(Z + base);
+            double2 *sA2 = reinterpret_cast<double2 *>(sA);
+            double2 *sB2 = reinterpret_cast<double2 *>(sB);
+            double2 *sZ2 = reinterpret_cast<double2 *>(sZ);
+            for (int i = t; i < 3 * kTile / 2; i += kTile) {
+                sA2[i] = __ldg(A2 + i);
+                sB2[i] = __ldg(B2 + i);
+            }
+            if (t < kTile / 2) sZ2[t] = __ldg(Z2 + t);
+        } else {
+            for (int i = t; i < 3 * cnt; i += kTile) {
+                sA[i] = A[3 * base + i];
+                sB[i] = B[3 * base + i];
+            }
+            if (t < cnt) sZ[t] = Z[base + t];
+        }
+        __syncthreads();
+        if constexpr (Mode == kAdaptive) {
+            bool pending = false;
+            if (t < cnt) {
+                const double x1[3] = {sA[3 * t], sA[3 * t + 1], sA[3 * t + 2]};
+                const double x2[3] = {sB[3 * t], sB[3 * t + 1], sB[3 * t + 2]};
+                PairOut o;
+                if (filt::pair_filtered(x1, x2, sZ[t], gate, o))
+                    stage_result(t, o, sZ[t]);
+                else
+                    pending = true;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pending);
+            if (m) {
+                const int lane = t & 31, leader = __ffs(m) - 1;
+                int at = 0;
+                if (lane == leader) at = atomicAdd(&sQn, __popc(m));
+                at = __shfl_sync(0xffffffffu, at, leader);
+                if (pending) sQ[at + __popc(m & ((1u << lane) - 1u))] = t;
+            }
+            __syncthreads();
+            const int qn = sQn;
+            if (t < qn) {
+                const int j = sQ[t];
+                const double x1[3] = {sA[3 * j], sA[3 * j + 1], sA[3 * j + 2]};
+                const double x2[3] = {sB[3 * j], sB[3 * j + 1], sB[3 * j + 2]};
+                PairOut o;
+                pair_wide(x1, x2, sZ[j], o);
+                stage_result(j, o, sZ[j]);
+            }
+            if (fallback && t == 0 && qn) atomicAdd(fallback, (unsigned long long)qn);
+        } else {
+            if (t < cnt) {
+                const double x1[3] = {sA[3 * t], sA[3 * t + 1], sA[3 * t + 2]};
+                const double x2[3] = {sB[3 * t], sB[3 * t + 1], sB[3 * t + 2]};
+                PairOut o;
+                intersect_pair<Mode>(x1, x2, sZ[t], o);
+                stage_result(t, o, sZ[t]);
+            }
+        }
+        __syncthreads();
+        if (cnt == kTile) {
+            double2 *P2 = reinterpret_cast<double2 *>(out_pts + 6 * base);
+            const double2 *sP2 = reinterpret_cast<const double2 *>(sP);
+            for (int i = t; i < 3 * kTile; i += kTile) P2[i] = sP2[i];
+            int4 *C4 = reinterpret_cast<int4 *>(out_count + base);
+            if (t < kTile / 4) C4[t] = reinterpret_cast<const int4 *>(sC)[t];
+        } else {
+            for (int i = t; i < 6 * cnt; i += kTile) out_pts[6 * base + i] = sP[i];
+            if (t < cnt) out_count[base + t] = sC[t];
+        }
+        __syncthreads();
+    }
+}
+
+static inline int sm_count_of_current() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// resident blocks per SM of dense_kernel<Mode> (its registers decide)
+template <int Mode>
+static int resident_blocks() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dense_kernel<Mode>, kTile, 0) !=
+            cudaSuccess ||
+        b < 1) {
+        cudaGetLastError();
+        b = 4;
+    }
+    return b;
+}
+
+template <int Mode>
+static void launch_dense(const double *A, const double *B, const double *Z, int64_t n,
+                         double *P, int32_t *C, cudaStream_t s,
+                         unsigned long long *fallback = nullptr, double gate_ulps = 4.0) {
+    static const int sms = sm_count_of_current();
+    static const int per_sm = resident_blocks<Mode>();
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    // exactly one wave of resident blocks: a second, partial wave would leave
+    // most SMs idle while it finishes
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+    dense_kernel<Mode><<<(unsigned)grid, kTile, 0, s>>>(A, B, Z, n, P, C, fallback,
+                                                        0.975 * gate_ulps);
+}
+
+// the adaptive mode's launcher (adaptive.cu)
+void launch_adaptive(const double *A, const double *B, const double *Z, int64_t n, double *P,
+                     int32_t *C, double gate_ulps, unsigned long long *fallback, cudaStream_t s);
+
+}  // namespace sphx

@@ -75,6 +75,7 @@ extern "C" sphx_status sphx_intersect_ragged_noalloc(const double *A, const doub
                                                      sphx_stream stream) {
     if (M < 1 || E < 0 || L < 0 || L > INT32_MAX || out_cap < 0) return SPHX_ERR_INVALID_ARG;
     if (E > kNoAllocMaxEdges) return SPHX_ERR_INVALID_ARG;  // beyond the fixed scratch
+    if (mode == SPHX_MODE_ADAPTIVE) return SPHX_ERR_UNSUPPORTED;
     if ((int)mode < 0 || (int)mode > 4) return SPHX_ERR_INVALID_ARG;
     if (!out_total || (out_cap > 0 && !out)) return SPHX_ERR_INVALID_ARG;
     if (E > 0 && (!A || !B || !edge_offsets || !lat_z || !lat_offsets)) return SPHX_ERR_INVALID_ARG;

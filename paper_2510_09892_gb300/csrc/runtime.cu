@@ -253,6 +253,7 @@ cudaError_t enqueue_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedS
 
 sphx_status check_ragged_args(const RaggedCall &c) {
     if (c.M < 1 || c.E < 0 || c.L < 0 || c.L > INT32_MAX || c.cap < 0) return SPHX_ERR_INVALID_ARG;
+    if (c.mode == SPHX_MODE_ADAPTIVE) return SPHX_ERR_UNSUPPORTED;
     if (c.mode < 0 || c.mode > 4) return SPHX_ERR_INVALID_ARG;
     if (!c.out_total || (c.cap > 0 && !c.out)) return SPHX_ERR_INVALID_ARG;
     if ((c.lo == nullptr) != (c.hi == nullptr)) return SPHX_ERR_INVALID_ARG;
@@ -477,7 +478,7 @@ sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A,
     if (!ctx || n < 0) return SPHX_ERR_INVALID_ARG;
     if (n == 0) return SPHX_OK;
     if (!A || !B || !z0 || !out_pts || !out_count) return SPHX_ERR_INVALID_ARG;
-    if ((int)mode < 0 || (int)mode > 4) return SPHX_ERR_INVALID_ARG;
+    if ((int)mode < 0 || (int)mode > 5) return SPHX_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
     if (mapped_host(A, n * 3 * sizeof(double)) && mapped_host(B, n * 3 * sizeof(double)) &&

@@ -20,9 +20,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sphx.h")
 # sphx_status
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = range(7)
 # sphx_mode
-MODE_DIRECT_FP64, MODE_EFT_FP64, MODE_EFT_FF32, MODE_EFT_FP64_PRINTED, MODE_WIDE_INT = range(5)
+(MODE_DIRECT_FP64, MODE_EFT_FP64, MODE_EFT_FF32, MODE_EFT_FP64_PRINTED, MODE_WIDE_INT,
+ MODE_ADAPTIVE) = range(6)
 MODES = {"direct": MODE_DIRECT_FP64, "eft": MODE_EFT_FP64, "ff32": MODE_EFT_FF32,
-         "eft_printed": MODE_EFT_FP64_PRINTED, "wide": MODE_WIDE_INT}
+         "eft_printed": MODE_EFT_FP64_PRINTED, "wide": MODE_WIDE_INT, "adaptive": MODE_ADAPTIVE}
 # sphx_compaction
 COMPACT_AUTO, COMPACT_ATOMIC, COMPACT_ORDERED = range(3)
 
@@ -54,6 +55,8 @@ _SIGS = {
     "sphx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
     "sphx_destroy": (None, [_vp]),
     "sphx_intersect_gca_constlat": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp]),
+    "sphx_intersect_gca_constlat_adaptive": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp,
+                                                            ctypes.c_double, _vp, _vp]),
     "sphx_intersect_gca_constlat_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp,
                                                         ctypes.c_int, _vp]),
     "sphx_host_join": (ctypes.c_int, [_vp, _vp]),
@@ -170,6 +173,25 @@ def sphx_intersect_gca_constlat(A, B, z0, out_pts, out_count, mode="eft", stream
     st = lib().sphx_intersect_gca_constlat(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_pts),
                                            _ptr(out_count), _mode(mode), _stream(stream))
     _check(st, "sphx_intersect_gca_constlat")
+
+
+def sphx_intersect_gca_constlat_adaptive(A, B, z0, out_pts, out_count, gate_ulps=4.0,
+                                         fallback_count=None, stream=None):
+    """The dense call in the adaptive mode with a gate of gate_ulps ulp per
+    component; fallback_count: optional (1,) int64 CUDA tensor to which the
+    number of arcs re-evaluated by the accurate form is added."""
+    n = int(z0.shape[0])
+    _dev_tensor(A, torch.float64, "A", (n, 3))
+    _dev_tensor(B, torch.float64, "B", (n, 3))
+    _dev_tensor(z0, torch.float64, "z0", (n,))
+    _dev_tensor(out_pts, torch.float64, "out_pts", (n, 2, 3))
+    _dev_tensor(out_count, torch.int32, "out_count", (n,))
+    if fallback_count is not None:
+        _dev_tensor(fallback_count, torch.int64, "fallback_count", (1,))
+    st = lib().sphx_intersect_gca_constlat_adaptive(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_pts),
+                                                    _ptr(out_count), float(gate_ulps),
+                                                    _ptr(fallback_count), _stream(stream))
+    _check(st, "sphx_intersect_gca_constlat_adaptive")
 
 
 def sphx_intersect_gca_gca(A1, A2, B1, B2, out_pts, out_count, mode="wide", stream=None):

@@ -41,6 +41,25 @@ def test_dense_argument_errors_before_launch():
     assert f(FAKE, FAKE, FAKE, 10, FAKE, FAKE + 4, 1, None) == sphx.ERR_INVALID_ARG
     assert f(FAKE, FAKE, FAKE, 10, FAKE, FAKE, 7, None) == sphx.ERR_INVALID_ARG
     assert f(None, None, None, 0, None, None, 1, None) == sphx.OK  # n = 0: no-op
+    h = L.sphx_intersect_gca_constlat_adaptive
+    assert h(FAKE, FAKE, FAKE, -1, FAKE, FAKE, 4.0, None, None) == sphx.ERR_INVALID_ARG
+    assert h(FAKE, None, FAKE, 10, FAKE, FAKE, 4.0, None, None) == sphx.ERR_INVALID_ARG
+    assert h(FAKE, FAKE, FAKE, 10, FAKE + 8, FAKE, 4.0, None, None) == sphx.ERR_INVALID_ARG
+    assert h(FAKE, FAKE, FAKE, 10, FAKE, FAKE, 4.0, FAKE + 4, None) == sphx.ERR_INVALID_ARG
+    for gate in (0.5, float("nan"), 2.0 ** 27):
+        assert h(FAKE, FAKE, FAKE, 10, FAKE, FAKE, gate, None, None) == sphx.ERR_INVALID_ARG
+    assert h(None, None, None, 0, None, None, 4.0, None, None) == sphx.OK
+
+
+def test_adaptive_mode_is_dense_only():
+    """The ragged and arc x arc calls refuse the adaptive mode before launching."""
+    L = sphx.lib()
+    ctx = ctypes.c_void_p(FAKE)
+    st = L.sphx_intersect_ragged(ctx, FAKE, FAKE, FAKE, 1, 10, FAKE, FAKE, 5, None, None,
+                                 sphx.MODE_ADAPTIVE, FAKE, 10, FAKE, None)
+    assert st == sphx.ERR_UNSUPPORTED
+    st = L.sphx_intersect_gca_gca(FAKE, FAKE, FAKE, FAKE, 10, FAKE, FAKE, sphx.MODE_ADAPTIVE, None)
+    assert st == sphx.ERR_UNSUPPORTED
 
 
 def test_ragged_argument_errors_before_launch():

@@ -89,23 +89,29 @@ def test_eft_stress_mix_within_4ulp_and_direct_worse():
     assert np.nanmax(np.where(both, P.norm_error(pd, pe, z), 0)) > 1e3
 
 
+def gen_arcs(gen):
+    """Well-conditioned, ill-conditioned, mixed and non-unit seeded inputs."""
+    if gen == "uniform":
+        return W.uniform_arcs(10_000, seed=41)
+    if gen == "stress":
+        return W.stress_arcs(40_000, seed=42)
+    if gen == "mixed":
+        return W.mixed_chunk(7, size=20_000)
+    # endpoints scaled by 10^+-30: the formula only uses directions
+    A, B, z = W.stress_arcs(20_000, seed=43)
+    rng = np.random.default_rng(44)
+    A = A * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    B = B * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    return A, B, z
+
+
 @pytest.mark.parametrize("gen", ["uniform", "stress", "mixed", "scaled"])
 def test_wide_int_matches_exact_oracle(gen):
     """The integer-limb evaluation: exact hit counts on unflagged arcs and
     every coordinate within 1 ulp of the correctly rounded exact value (the
     4-ulp bound with room to spare: 96-bit mantissas leave the rounding to
     decide), on well-conditioned, ill-conditioned, mixed and non-unit inputs."""
-    if gen == "uniform":
-        A, B, z = W.uniform_arcs(10_000, seed=41)
-    elif gen == "stress":
-        A, B, z = W.stress_arcs(40_000, seed=42)
-    elif gen == "mixed":
-        A, B, z = W.mixed_chunk(7, size=20_000)
-    else:  # endpoints scaled by 10^+-30: the formula only uses directions
-        A, B, z = W.stress_arcs(20_000, seed=43)
-        rng = np.random.default_rng(44)
-        A = A * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
-        B = B * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    A, B, z = gen_arcs(gen)
     cnt, pts = run(A, B, z, "wide")
     ce, pe, fe = check_against_exact(cnt, pts, A, B, z, ulp_gate=1.0)
     ok = (fe == 0)[:, None] & np.isfinite(pe[..., 0])
@@ -127,6 +133,68 @@ def test_wide_int_full_size_stress_sampled():
     both = np.isfinite(pts[..., 0]) & np.isfinite(pe[..., 0]) & same[:, None]
     _, _, gate = P.component_errors(pe, pts, z)
     assert np.nanmax(np.where(both[..., None], gate, 0)) <= 5.0
+
+
+def run_adaptive(A, B, z, fallback=None, gate=4.0):
+    dev = torch.device("cuda:0")
+    tA, tB, tz = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (A, B, z))
+    pts = torch.full((len(z), 2, 3), 7.0, dtype=torch.float64, device=dev)  # poison
+    cnt = torch.full((len(z),), -99, dtype=torch.int32, device=dev)
+    fb = torch.zeros(1, dtype=torch.int64, device=dev) if fallback is None else fallback
+    sphx.sphx_intersect_gca_constlat_adaptive(tA, tB, tz, pts, cnt, gate, fb)
+    torch.cuda.synchronize()
+    return cnt.cpu().numpy(), pts.cpu().numpy(), int(fb.item())
+
+
+def check_adaptive(gen, gate):
+    """Every arc within the gate and with the exact hit count on unflagged
+    arcs. Arcs the filter hands on are evaluated by the integer-limb form, so
+    an arc whose result differs from that form in any bit was kept by the
+    filter: those must have the exact hit count even where the oracle flags a
+    near-boundary case, and their number cannot exceed the arcs the filter
+    kept. Returns the share of arcs the filter kept."""
+    A, B, z = gen_arcs(gen)
+    cnt, pts, fb = run_adaptive(A, B, z, gate=gate)
+    cw, pw = run(A, B, z, "wide")
+    ce, pe, fe = check_against_exact(cnt, pts, A, B, z, ulp_gate=gate)
+    bits = lambda p: np.where(np.isnan(p), 0.0, p).view(np.int64)
+    kept = (cnt != cw) | (bits(pts) != bits(pw)).any(axis=(1, 2))
+    assert 0 <= fb <= len(z) and kept.sum() <= len(z) - fb
+    assert np.array_equal(cnt[kept], ce[kept])
+    hit = np.isfinite(pe[kept][..., 0])
+    _, _, g = P.component_errors(pts[kept], pe[kept], z[kept])
+    assert np.nanmax(np.where(hit[..., None], g, 0.0), initial=0.0) <= gate
+    share = 1 - fb / len(z)
+    print(f"{gen}, gate {gate:g} ulp: filter kept {share:.3f} of {len(z)} arcs, "
+          f"{kept.mean():.3f} differ from the integer-limb result")
+    return share
+
+
+@pytest.mark.parametrize("gen", ["uniform", "stress", "mixed", "scaled"])
+def test_adaptive_filter_within_4ulp(gen):
+    """The adaptive mode at its own gate (4 ulp per component)."""
+    check_adaptive(gen, 4.0)
+
+
+@pytest.mark.parametrize("gen,gate,min_kept", [("uniform", 64.0, 0.3), ("mixed", 64.0, 0.2),
+                                               ("stress", 2.0 ** 20, 0.08)])
+def test_adaptive_filter_relaxed_gates(gen, gate, min_kept):
+    """Looser gates let the filter keep many arcs, which tests its bound: the
+    kept arcs of well-conditioned and of ill-conditioned inputs must keep
+    exact hit counts and stay within the gate against the exact oracle."""
+    assert check_adaptive(gen, gate) >= min_kept
+
+
+def test_adaptive_fallback_counter_accumulates():
+    A, B, z = W.stress_arcs(3000, seed=17)
+    fb = torch.zeros(1, dtype=torch.int64, device=torch.device("cuda:0"))
+    c1, p1, f1 = run_adaptive(A, B, z, fb)
+    c2, p2, f2 = run_adaptive(A, B, z, fb)
+    assert 0 < f1 <= len(z) and f2 == 2 * f1
+    assert np.array_equal(c1, c2) and P.same_bits(p1, p2)
+    # the plain dense call in the adaptive mode gives the same results
+    c3, p3 = run(A, B, z, "adaptive")
+    assert np.array_equal(c1, c3) and P.same_bits(p1, p3)
 
 
 @pytest.mark.parametrize("gen", ["uniform", "stress"])
@@ -170,7 +238,7 @@ def test_edge_cases():
     z = np.array([r[2] for r in rows], dtype=np.float64)
     from oracle import exact
     want = np.array([exact.intersect(A[i], B[i], z[i]).count for i in range(len(z))])
-    for mode in ("eft", "direct", "ff32", "wide"):
+    for mode in ("eft", "direct", "ff32", "wide", "adaptive"):
         cnt, pts = run(A, B, z, mode)
         # degenerate, non-finite and equator cases are exact decisions in every mode
         assert np.array_equal(cnt[:6], want[:6]), (mode, cnt, want)
@@ -179,7 +247,7 @@ def test_edge_cases():
         filled = np.isfinite(pts).all(axis=2).sum(axis=1)
         assert np.array_equal(filled, np.maximum(cnt, 0))
         assert (np.isfinite(pts).all(axis=2) | np.isnan(pts).all(axis=2)).all()
-    for mode in ("eft", "wide"):
+    for mode in ("eft", "wide", "adaptive"):
         cnt, pts = run(A, B, z, mode)
         assert np.array_equal(cnt, want), mode
 
