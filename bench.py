@@ -52,7 +52,7 @@ INST_PER_ARC = {"wide": 2423}
 # DRAM bytes (read + write) of one launch of the headline kernel over the 10^6
 # stress arcs, from the same ncu capture (writes still in L2 at kernel end are
 # not counted)
-TRAFFIC_PER_LAUNCH = {"wide": 56.056e6 + 8.937e6}
+TRAFFIC_PER_LAUNCH = {"wide": 56.056e6 + 8.354e6}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
