@@ -86,7 +86,7 @@ SPHX_HD bool finite12(const double (&a1)[3], const double (&a2)[3], const double
 
 // ---- integer limbs -------------------------------------------------------------
 // n_a, n_b exact (106-bit products, 128-bit differences), v = n_a x n_b and
-// |v|^2 with 128-bit mantissas, 1 / |v| from the FP64-seeded square root and
+// |v|^2 with 128-bit mantissas, 1 / |v| from the integer-limb square root and
 // reciprocal (96 bits), p_i = v_i / |v| rounded to nearest
 SPHX_HD void arcs_wide(const double (&a1)[3], const double (&a2)[3], const double (&b1)[3],
                        const double (&b2)[3], ArcOut &r) {
@@ -123,7 +123,7 @@ SPHX_HD void arcs_wide(const double (&a1)[3], const double (&a2)[3], const doubl
         return;
     }
     const W<4> S = add_same<4>(add_same<4>(sqr<4>(v[0]), sqr<4>(v[1])), sqr<4>(v[2]));
-    const W<3> inv = recip_fast<3>(sqrt_fast<3>(narrow<4, 3>(S)));
+    const W<3> inv = recip_int<3>(sqrt_int<3>(narrow<4, 3>(S)));
     const double p[3] = {to_double<3>(mul<3>(narrow<4, 3>(v[0]), inv)),
                          to_double<3>(mul<3>(narrow<4, 3>(v[1]), inv)),
                          to_double<3>(mul<3>(narrow<4, 3>(v[2]), inv))};

@@ -296,9 +296,9 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
     // P_xy = g n_xy + sigma h (n_y, -n_x) with g = -z0 n_z / |n_xy|^2 and
     // h = -s / |n_xy|^2: Eq. 2.2 with the division distributed
     const W<3> nx = narrow<4, 3>(n[0]), ny = narrow<4, 3>(n[1]), nz = narrow<4, 3>(n[2]);
-    const W<3> rS2 = negate<3>(recip_fast<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
+    const W<3> rS2 = negate<3>(recip_int<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
     const W<3> g = mul<3>(mul<3>(from_double<3>(z0), nz), rS2);
-    const W<3> h = tangent ? zero<3>() : mul<3>(sqrt_fast<3>(narrow<4, 3>(s2)), rS2);
+    const W<3> h = tangent ? zero<3>() : mul<3>(sqrt_int<3>(narrow<4, 3>(s2)), rS2);
     const W<3> gx = mul<3>(g, nx), gy = mul<3>(g, ny);
     const W<3> hx = mul<3>(h, nx), hy = mul<3>(h, ny);
     W<3> Px_lin[2], Py_lin[2];  // both roots: g n_x +- h n_y and g n_y -+ h n_x

@@ -525,87 +525,151 @@ SPHX_HD float rsqrt32(float x) {
 #endif
 }
 
-// a double in [2^-126, 2^127) as a float (mantissa truncated), by its bits
-SPHX_HD float f32_of_f64(double x) {
-    const uint64_t b = bits_of(x);
-    const uint32_t hi = (uint32_t)(b >> 32);
-    const uint32_t fe = ((hi >> 20) & 0x7ffu) - 1023u + 127u;
-    return float_of((hi & 0x80000000u) | (fe << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+// high 64 bits of the 128-bit product a * b
+SPHX_HD uint64_t umul64hi(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
 }
 
-// a normal float as a double (exact), by its bits
-SPHX_HD double f64_of_f32(float f) {
-    const uint32_t b = fbits_of(f);
-    const uint64_t fe = ((b >> 23) & 0xffu) - 127u + 1023u;
-    return double_of(((uint64_t)(b & 0x80000000u) << 32) | (fe << 52) |
-                     ((uint64_t)(b & 0x7fffffu) << 29));
+// a 32-bit unsigned integer rounded to the nearest float
+SPHX_HD float f32_of_u32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+    return __uint2float_rn(x);
+#else
+    return (float)x;
+#endif
 }
 
-// the 96-bit mantissa of a (|a| in [1/4, 2)) as two doubles hi + lo, exactly:
-// hi holds the top 53 bits (truncated), lo the remaining 43
-SPHX_HD void to_dd(const W<3> &a, double &hi, double &lo) {
-    const uint64_t t = ((uint64_t)a.m[2] << 32) | a.m[1];
-    const uint64_t sign = (uint64_t)a.neg << 63;
-    hi = double_of(sign | ((uint64_t)(a.e + 1022) << 52) | ((t >> 11) & ((1ull << 52) - 1)));
-    const uint64_t R = ((uint64_t)(a.m[1] & 0x7ffu) << 32) | a.m[0];
-    if (R == 0) {
-        lo = 0.0;
-        return;
+// R = r 2^31 for an FP32 r in [1, 2] (2 itself saturates to 2^32 - 1)
+SPHX_HD uint32_t fixed31_of(float r) {
+    const uint32_t b = fbits_of(r);
+    return (b >> 23) == 127u ? (((b & 0x7fffffu) | 0x800000u) << 8) : 0xffffffffu;
+}
+
+// R r / 2^32 for a signed residual r (|r| < 2^63) and R < 2^32, truncated toward 0
+SPHX_HD int64_t mul_fixed31(uint32_t R, int64_t r) {
+    const uint64_t m = r < 0 ? (uint64_t)0 - (uint64_t)r : (uint64_t)r;
+    const uint64_t p = (uint64_t)R * (uint32_t)(m >> 32) + (((uint64_t)R * (uint32_t)m) >> 32);
+    return r < 0 ? -(int64_t)p : (int64_t)p;
+}
+
+// the 96-bit value (hi:lo64) plus a signed 64-bit amount, as limbs; the
+// result is clamped to 2^96 - 1 on a carry out (callers' values stay below 2^96
+// except by rounding-size amounts)
+SPHX_HD void add_signed96(uint32_t (&m)[3], uint32_t hi, uint64_t lo, int64_t d) {
+    uint64_t l2 = lo + (uint64_t)d;
+    uint32_t h2 = hi;
+    if (d >= 0) {
+        if (l2 < lo) {
+            if (++h2 == 0u) {
+                m[0] = m[1] = m[2] = 0xffffffffu;
+                return;
+            }
+        }
+    } else if (l2 > lo) {
+        --h2;
     }
-    int lz = clz32((uint32_t)(R >> 32));
-    if (lz == 32) lz += clz32((uint32_t)R);
-    const int bl = 64 - lz;  // R = 0.R' 2^bl
-    lo = double_of(sign | ((uint64_t)(a.e - 96 + bl + 1022) << 52) |
-                   ((R << (53 - bl)) & ((1ull << 52) - 1)));
+    m[0] = (uint32_t)l2;
+    m[1] = (uint32_t)(l2 >> 32);
+    m[2] = h2;
 }
 
-// hi + lo (|lo| well below |hi|) as a W<K>
+// 1 / a for a != 0 to about 2^-91, on the integer pipe. With f = 0.M in
+// [1/2, 1) the mantissa of a (M = m2 m1 m0): an FP32 seed r0 ~ 1/f from f
+// rounded to 24 bits (1 - f r0 within 2^-23), then two Newton steps
+// r <- r + r (1 - f r) in fixed point (r0 2^31, r1 2^62, r2 2^94). Each
+// residual 1 - f r is small, so it is read from the middle limbs of f r: the
+// bits of 2^k - f r 2^k above a limb boundary, taken modulo 2^64, are the
+// residual as a signed 64-bit number (the borrow from the dropped low limbs
+// is below one unit). Relative error: the second residual squared
+// (<= 2^-92) plus truncations of a few units of 2^-94.
 template <int K>
-SPHX_HD W<K> from_dd(double hi, double lo) {
-    return add<K>(from_double<K>(hi), from_double<K>(lo));
-}
-
-// sqrt(a) for a > 0 to about 2^-90: with a = f 2^(2h), f = fh + fl in
-// [1/4, 1): an FP32 seed y0 ~ 1/sqrt(fh) (2^-24), one FP64 Newton step
-// y = y0 + y0 (1 - fh y0^2) / 2 (2^-46), d = fh y, then one exact-residual
-// step sqrt(f) = d + (f - d^2) y / 2, with f - d^2 = fma(-d, d, fh) + fl
-template <int K>
-SPHX_HD W<K> sqrt_fast(const W<K> &a) {
-    static_assert(K == 3, "sqrt_fast works on 96-bit mantissas");
-    W<3> f = a;
-    const int odd = a.e & 1;
-    f.e = -odd;
-    f.neg = 0u;
-    const int h = (a.e + odd) / 2;
-    double fh, fl;
-    to_dd(f, fh, fl);
-    const double y0 = f64_of_f32(rsqrt32(f32_of_f64(fh)));
-    const double y = fma64(0.5 * y0, fma64(-fh * y0, y0, 1.0), y0);
-    const double d = fh * y;
-    const double res = fma64(-d, d, fh) + fl;
-    W<3> s = from_dd<3>(d, res * (0.5 * y));
-    s.e += h;
-    return s;
-}
-
-// 1 / a for a != 0 to about 2^-90: with f = fh + fl the mantissa of a in
-// [1/2, 1): an FP32 seed r0 ~ 1 / fh, one FP64 Newton step r = r0 + r0 (1 - fh r0)
-// (2^-46), then 1 / f = r (1 + e) + O(e^2) with e = (1 - fh r) - fl r
-template <int K>
-SPHX_HD W<K> recip_fast(const W<K> &a) {
-    static_assert(K == 3, "recip_fast works on 96-bit mantissas");
-    W<3> f = a;
-    f.e = 0;
-    f.neg = 0u;
-    double fh, fl;
-    to_dd(f, fh, fl);
-    const double r0 = f64_of_f32(rcp32(f32_of_f64(fh)));
-    const double r = fma64(r0, fma64(-fh, r0, 1.0), r0);
-    const double e = fma64(-fl, r, fma64(-fh, r, 1.0));
-    W<3> q = from_dd<3>(r, r * e);
-    q.e -= a.e;
+SPHX_HD W<K> recip_int(const W<K> &a) {
+    static_assert(K == 3, "recip_int works on 96-bit mantissas");
+    const uint32_t m0 = a.m[0], m1 = a.m[1], m2 = a.m[2];
+    W<3> q;
     q.neg = a.neg;
+    if (m2 == 0x80000000u && (m1 | m0) == 0u) {  // f = 1/2: 1/f = 2 exactly
+        q.m[0] = q.m[1] = 0u;
+        q.m[2] = 0x80000000u;
+        q.e = 2 - a.e;
+        return q;
+    }
+    // seed: f rounded to 24 bits, t in [2^23, 2^24], as the float t 2^-24
+    const uint32_t t = (m2 >> 8) + ((m2 >> 7) & 1u);
+    const uint32_t R0 = fixed31_of(rcp32(float_of(0x3e800000u + t)));  // r0 2^31
+    // step 1: f r0 = M R0 2^-127; bits 64.. of 2^127 - M R0 give e0 2^63
+    const uint64_t p0 = (uint64_t)m0 * R0, p1 = (uint64_t)m1 * R0, p2 = (uint64_t)m2 * R0;
+    const uint64_t mid = (p0 >> 32) + (uint32_t)p1;
+    const uint64_t T1 = p2 + (p1 >> 32) + (mid >> 32);
+    const int64_t e0 = (int64_t)(0x8000000000000000ull - T1);
+    const uint64_t R1 = ((uint64_t)R0 << 31) + (uint64_t)mul_fixed31(R0, e0);  // r1 2^62
+    // step 2: f r1 = M R1 2^-158; bits 64..127 of 2^158 - M R1 give e1 2^94
+    const uint32_t rl = (uint32_t)R1, rh = (uint32_t)(R1 >> 32);
+    const uint64_t a0 = (uint64_t)m0 * rl, a1 = (uint64_t)m0 * rh, b0 = (uint64_t)m1 * rl;
+    const uint64_t b1 = (uint64_t)m1 * rh, c0 = (uint64_t)m2 * rl, c1 = (uint64_t)m2 * rh;
+    const uint64_t col1 = (a0 >> 32) + (uint32_t)a1 + (uint32_t)b0;  // bits 32.. (< 3 2^32)
+    const uint64_t T2 = b1 + c0 + (c1 << 32) + (a1 >> 32) + (b0 >> 32) + (col1 >> 32);
+    const int64_t e1 = (int64_t)(0ull - T2);
+    // r2 = r1 + r1 e1 = R1 2^32 + R1 e1 2^-62 (units of 2^-94)
+    const uint64_t u = e1 < 0 ? (uint64_t)0 - (uint64_t)e1 : (uint64_t)e1;
+    const uint64_t corr = (umul64hi(R1, u) << 2) | ((R1 * u) >> 62);
+    add_signed96(q.m, rh, (uint64_t)rl << 32, e1 < 0 ? -(int64_t)corr : (int64_t)corr);
+    const int sh = normalize_mant<3>(q.m);  // r2 2^94 -> 0.Q: 1 / a = 0.Q 2^(2 - sh - e)
+    q.e = 2 - sh - a.e;
     return q;
+}
+
+// sqrt(a) for a > 0 to about 2^-91, on the integer pipe. With a = f 2^(2h),
+// f in [1/4, 1) (M shifted right by one bit when the exponent is odd): an
+// FP32 seed y0 ~ 1/sqrt(f), one Newton step y1 = y0 + y0 (1 - f y0^2) / 2
+// (about 2^-46) in fixed point, d = f y1 truncated to 64 bits, the residual
+// f - d^2 exactly in 128 bits, and sqrt(f) = d + (f - d^2) y1 / 2, whose
+// error is about twice the square of y1's.
+template <int K>
+SPHX_HD W<K> sqrt_int(const W<K> &a) {
+    static_assert(K == 3, "sqrt_int works on 96-bit mantissas");
+    const int odd = a.e & 1;
+    const int h = (a.e + odd) / 2;
+    // F = f 2^96
+    const uint32_t f0 = odd ? funnel_r(a.m[0], a.m[1], 1) : a.m[0];
+    const uint32_t f1 = odd ? funnel_r(a.m[1], a.m[2], 1) : a.m[1];
+    const uint32_t f2 = odd ? (a.m[2] >> 1) : a.m[2];
+    // seed: the top limb rounded to a float and scaled by 2^-32 (exact)
+    const uint32_t Y0 = fixed31_of(rsqrt32(f32_of_u32(f2) * 2.3283064365386963e-10f));  // y0 2^31
+    // step 1: F Y0^2 = f y0^2 2^158; its bits 96.. are f y0^2 2^62 (lower
+    // partial products dropped: a few units)
+    const uint64_t Q = (uint64_t)Y0 * Y0;  // y0^2 2^62 < 2^64
+    const uint32_t ql = (uint32_t)Q, qh = (uint32_t)(Q >> 32);
+    const uint64_t TT = (uint64_t)f2 * qh + (((uint64_t)f1 * qh) >> 32) + (((uint64_t)f2 * ql) >> 32);
+    const int64_t g = (int64_t)(0x4000000000000000ull - TT);  // (1 - f y0^2) 2^62
+    const uint64_t Y1 = ((uint64_t)Y0 << 31) + (uint64_t)mul_fixed31(Y0, g);  // y1 2^62
+    // d 2^64 = F Y1 2^-94 (bits 94.. of the product; clamped below 1)
+    const uint32_t yl = (uint32_t)Y1, yh = (uint32_t)(Y1 >> 32);
+    const uint64_t top = (uint64_t)f2 * yh;
+    const uint64_t D0 = top << 2;
+    uint64_t D = D0 + (((uint64_t)f2 * yl) >> 30) + (((uint64_t)f1 * yh) >> 30);
+    if ((top >> 62) != 0u || D < D0) D = ~0ull;
+    // (f - d^2) 2^128 = F 2^32 - D^2, exact modulo 2^128; |f - d^2| < 2^-45,
+    // so bits 30..93 hold it as a signed 64-bit number (units of 2^-98)
+    const uint64_t dl = D * D, dh = umul64hi(D, D);
+    const uint64_t al = (uint64_t)f0 << 32, ah = ((uint64_t)f2 << 32) | f1;
+    const uint64_t rl = al - dl;
+    const uint64_t rh = ah - dh - (al < dl ? 1u : 0u);
+    const int64_t rho = (int64_t)((rh << 34) | (rl >> 30));
+    // sqrt(f) 2^96 = D 2^32 + rho Y1 2^-65
+    const uint64_t u = rho < 0 ? (uint64_t)0 - (uint64_t)rho : (uint64_t)rho;
+    const uint64_t corr = umul64hi(u, Y1) >> 1;
+    W<3> r;
+    add_signed96(r.m, (uint32_t)(D >> 32), (uint64_t)(uint32_t)D << 32,
+                 rho < 0 ? -(int64_t)corr : (int64_t)corr);
+    const int sh = normalize_mant<3>(r.m);
+    r.e = h - sh;
+    r.neg = 0u;
+    return r;
 }
 
 // s = a + b and d = a - b, sharing the alignment
