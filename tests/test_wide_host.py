@@ -1,0 +1,145 @@
+"""The integer-limb arithmetic of the headline kernel, built for the host, against
+exact rationals (no GPU).
+
+The 96-bit routines the intersection formula relies on must meet the error
+bounds the kernel's accuracy argument uses:
+  * the reciprocal and the square root (FP32 seed, fixed-point Newton steps
+    with residuals read from the products' middle limbs) within 2^-92 relative;
+  * products (top limbs kept) and sums (truncating alignment) within a few
+    units of 2^-96 relative to their operands;
+  * the conversion to FP64 rounds to nearest, ties to even, exactly.
+Seeded random mantissas plus the edge cases of each routine: f = 1/2, f just
+below 1, mantissas next to the FP32 seed's rounding steps, odd and even
+exponents, cancellation in sums.
+"""
+import ctypes
+import os
+import random
+import shutil
+import subprocess
+from fractions import Fraction as F
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "wide_host_harness.cpp")
+OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "wide_host_harness.so")
+TOP = 1 << 95
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-o", OUT, SRC], check=True)
+    L = ctypes.CDLL(OUT)
+    u3 = ctypes.POINTER(ctypes.c_uint32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.h_recip.argtypes = [u3, ctypes.c_int, ctypes.c_int, u3, ip, ip]
+    L.h_sqrt.argtypes = [u3, ctypes.c_int, u3, ip, ip]
+    for f in (L.h_mul, L.h_add):
+        f.argtypes = [u3, ctypes.c_int, ctypes.c_int, u3, ctypes.c_int, ctypes.c_int, u3, ip, ip]
+    L.h_to_double.argtypes = [u3, ctypes.c_int, ctypes.c_int]
+    L.h_to_double.restype = ctypes.c_double
+    return L
+
+
+def limbs(M):
+    return (ctypes.c_uint32 * 3)(M & 0xffffffff, (M >> 32) & 0xffffffff, M >> 64)
+
+
+def value(M, e, neg=0):
+    v = F(M, 1 << 96) * F(2) ** e
+    return -v if neg else v
+
+
+def call(fn, *args):
+    r = (ctypes.c_uint32 * 3)()
+    e, n = ctypes.c_int(), ctypes.c_int()
+    fn(*args, r, ctypes.byref(e), ctypes.byref(n))
+    R = r[0] | (r[1] << 32) | (r[2] << 64)
+    return R, e.value, n.value
+
+
+def mantissas(rng, n):
+    out = [TOP, TOP + 1, (1 << 96) - 1, (1 << 96) - 2, TOP | (1 << 72), TOP + (1 << 71)]
+    for _ in range(200):  # next to the 24-bit seed's rounding steps
+        t = rng.randrange(1 << 23, 1 << 24)
+        out.append(min((1 << 96) - 1, max(TOP, (t << 72) + rng.randrange(-(1 << 66), 1 << 66))))
+    out += [rng.randrange(TOP, 1 << 96) for _ in range(n)]
+    return out
+
+
+def rel(got, exact):
+    return abs((got - exact) / exact)
+
+
+def test_reciprocal_within_2_pow_minus_92(lib):
+    rng = random.Random(20251009)
+    worst = 0
+    for M in mantissas(rng, 3000):
+        for e, neg in ((0, 0), (1, 1), (-37, 0), (600, 1)):
+            R, er, nr = call(lib.h_recip, limbs(M), e, neg)
+            assert R >> 95 == 1 and nr == neg
+            worst = max(worst, rel(value(R, er, nr), 1 / value(M, e, neg)))
+    assert worst <= F(1, 1 << 92), float(worst)
+    # 1/2 and 2 are exact
+    R, er, _ = call(lib.h_recip, limbs(TOP), 0, 0)
+    assert value(R, er) == 2
+
+
+def test_square_root_within_2_pow_minus_92(lib):
+    import math
+    rng = random.Random(20251010)
+    worst = 0
+    for M in mantissas(rng, 3000):
+        for e in (0, 1, -5, 8, -1021):
+            R, er, nr = call(lib.h_sqrt, limbs(M), e)
+            assert R >> 95 == 1 and nr == 0
+            a = value(M, e)
+            got = value(R, er)
+            # |got - sqrt(a)| = |got^2 - a| / (got + sqrt(a)), with sqrt(a) from an integer
+            # square root of a 2^p (p even, large enough to leave 150 bits)
+            t = e - 96
+            p = max(300, 300 - t)
+            p += p & 1
+            s = F(math.isqrt(M << (t + p)), 1 << (p // 2))
+            worst = max(worst, abs(got * got - a) / (got + s) / s)
+    assert worst <= F(1, 1 << 92), float(worst)
+    # perfect squares: 1/4 and its powers of four
+    for e in (0, 2, -40):
+        R, er, _ = call(lib.h_sqrt, limbs(TOP), e - 1)  # 2^(e - 2)
+        assert abs(value(R, er) - F(2) ** ((e - 2) // 2)) <= F(2) ** ((e - 2) // 2) / (1 << 92)
+
+
+def test_products_and_sums_within_a_few_units_of_2_pow_minus_96(lib):
+    rng = random.Random(7)
+    unit = F(1, 1 << 96)
+    for _ in range(3000):
+        A, B = rng.randrange(TOP, 1 << 96), rng.randrange(TOP, 1 << 96)
+        ea, eb = rng.randrange(-40, 40), rng.randrange(-40, 40)
+        na, nb = rng.randrange(2), rng.randrange(2)
+        a, b = value(A, ea, na), value(B, eb, nb)
+        R, er, nr = call(lib.h_mul, limbs(A), ea, na, limbs(B), eb, nb)
+        assert rel(value(R, er, nr), a * b) <= 8 * unit
+        R, er, nr = call(lib.h_add, limbs(A), ea, na, limbs(B), eb, nb)
+        # truncating alignment: within a few units of the larger operand
+        assert abs(value(R, er, nr) - (a + b)) <= 4 * unit * max(abs(a), abs(b))
+    # exact cancellation gives zero; near cancellation is exact
+    R, er, nr = call(lib.h_add, limbs(TOP + 5), 0, 0, limbs(TOP + 5), 0, 1)
+    assert R == 0
+    R, er, nr = call(lib.h_add, limbs(TOP + 5), 0, 0, limbs(TOP + 3), 0, 1)
+    assert value(R, er, nr) == F(2, 1 << 96)
+
+
+def test_conversion_to_double_rounds_to_nearest_even(lib):
+    rng = random.Random(11)
+    for _ in range(3000):
+        M = rng.randrange(TOP, 1 << 96)
+        if rng.random() < 0.3:  # exact ties and their neighbours
+            M = (M >> 43 << 43) | (1 << 42) | rng.choice([0, 0, 1])
+        e, neg = rng.randrange(-100, 100), rng.randrange(2)
+        got = lib.h_to_double(limbs(M), e, neg)
+        assert F(got) == F(float(value(M, e, neg)))  # Python rounds a Fraction to nearest even
