@@ -1,6 +1,6 @@
 // Per-pair intersection of one great circle arc (x1, x2) with one latitude
-// z = z0: Eq. 2.2 of arXiv 2510.09892 evaluated three ways (direct FP64,
-// AccuX in FP64, float-float), followed by the on-arc test.
+// z = z0: Eq. 2.2 of arXiv 2510.09892 evaluated four ways (direct FP64,
+// AccuX in FP64, float-float, integer limbs), followed by the on-arc test.
 //
 // Conventions (shared by every mode):
 //   count = -1  computed n = 0 (x1 parallel to x2), or n_xy = 0 and z0 = 0
@@ -189,10 +189,10 @@ __device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (
 // z0 n_x n_z +- s n_y, z0 n_y n_z -+ s n_x and the division by |n_xy|^2 follow
 // with 96-bit mantissas (every numerator term is at most sqrt(1 - z0^2)
 // |n_xy|^2 in magnitude, so 96 bits leave each coordinate within a fraction
-// of an ulp). The square root and the reciprocal start from correctly
-// rounded FP64 values (the only FP64 arithmetic besides the on-arc offsets)
-// refined by one exact correction on the limbs. Everything else runs on the
-// 32-bit integer pipe.
+// of an ulp). The square root and the reciprocal start from FP32 seeds and
+// are refined by fixed-point Newton steps on the limbs (recip_int, sqrt_int).
+// The only FP64 arithmetic left is the on-arc offsets; everything else runs
+// on the 32-bit integer pipe.
 //
 // On-arc test: t1 = (x1 x P).n = d1 . m1 with m1 = n x x1 and
 // d1 = P - l x1, l = +-1/|x1| (the sign of P . x1): x1 . m1 = 0, so any l
