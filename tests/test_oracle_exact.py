@@ -24,6 +24,7 @@ import numpy as np
 import pytest
 
 from oracle import exact
+from paper_2510_09892_gb300 import workloads as W
 
 getcontext().prec = 80
 
@@ -357,3 +358,89 @@ def test_planted_mistakes_are_caught(monkeypatch, mistake):
         except AssertionError:
             caught += 1
     assert caught >= 10
+
+
+# ------------------------------------------------- second implementation --
+# The same intersections derived differently, in exact rationals: a point of
+# the great circle is P = alpha x1 + beta x2 (the plane of the arc), so
+# alpha z1 + beta z2 = z0 and |P|^2 = 1, a quadratic in one unknown. The arc
+# holds P iff alpha >= 0 and beta >= 0 ((x1 x P).n = beta |n|^2 and
+# (P x x2).n = alpha |n|^2). Coordinates have the form (X + Y sqrt D) / Z and
+# are rounded by refining an integer square root until both ends of the
+# bracket round to the same double (float() of a Fraction rounds correctly).
+def _sign_surd(u, v, D):
+    """Sign of u + v sqrt(D) for rationals u, v and D >= 0."""
+    su = (u > 0) - (u < 0)
+    sv = (v > 0) - (v < 0) if D != 0 else 0
+    if su == sv or sv == 0:
+        return su
+    if su == 0:
+        return sv
+    d = u * u - v * v * D
+    return su if d > 0 else (sv if d < 0 else 0)
+
+
+def _round_surd(X, Y, D, Z):
+    """(X + Y sqrt D) / Z rounded to the nearest double (Z != 0)."""
+    import math
+    if Y == 0 or D == 0:
+        return float(X / Z)
+    k = 80
+    while True:
+        scale = 1 << k
+        n = D * scale * scale
+        r = math.isqrt(n.numerator // n.denominator)
+        lo, hi = Fraction(r, scale), Fraction(r + 2, scale)  # sqrt D in [lo, hi]
+        a = (X + Y * lo) / Z
+        b = (X + Y * hi) / Z
+        if float(a) == float(b):
+            return float(a)
+        k *= 2
+
+
+def _plane_basis_hits(x1, x2, z0):
+    a = [Fraction(v) for v in x1]
+    b = [Fraction(v) for v in x2]
+    z = Fraction(z0)
+    if b[2] == 0:  # solve for the other coefficient instead
+        pts = _plane_basis_hits(x2, x1, z0)
+        return pts
+    p0, p1 = z / b[2], -a[2] / b[2]  # beta = p0 + p1 alpha
+    w = [a[i] + p1 * b[i] for i in range(3)]  # P = p0 b + alpha w
+    ww = sum(c * c for c in w)
+    wb = sum(w[i] * b[i] for i in range(3))
+    bb = sum(c * c for c in b)
+    qa, qb, qc = ww, 2 * p0 * wb, p0 * p0 * bb - 1
+    D = qb * qb - 4 * qa * qc
+    if D < 0:
+        return []
+    out = []
+    for s in ((1,) if D == 0 else (1, -1)):
+        # alpha = (-qb + s sqrt D) / (2 qa), beta = p0 + p1 alpha
+        if _sign_surd(-qb, Fraction(s), D) < 0:
+            continue
+        if _sign_surd(2 * qa * p0 - p1 * qb, s * p1, D) < 0:
+            continue
+        pt = tuple(_round_surd(2 * qa * p0 * b[i] - qb * w[i], s * w[i], D, 2 * qa) for i in range(2))
+        out.append(pt)
+    return out
+
+
+def test_second_implementation_plane_basis():
+    """1000 seeded arcs (uniform and the stress mix): hit sets, bit for bit."""
+    A, B, z = W.uniform_arcs(600, seed=77)
+    A2, B2, z2 = W.stress_arcs(400, seed=78)
+    A, B, z = np.concatenate([A, A2]), np.concatenate([B, B2]), np.concatenate([z, z2])
+    checked = 0
+    for i in range(len(z)):
+        x1, x2, z0 = tuple(A[i]), tuple(B[i]), float(z[i])
+        if x1[2] == 0 and x2[2] == 0:
+            continue
+        r = exact.intersect(x1, x2, z0)
+        if r.count < 0:
+            continue
+        want = sorted(tuple(p[:2]) for p in r.pts if not np.isnan(p[0]))
+        got = sorted(_plane_basis_hits(x1, x2, z0))
+        assert len(got) == r.count and got == want, (i, got, want)
+        checked += 1
+    assert checked >= 990
