@@ -368,6 +368,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "ms_per_step_stats": {"mean": statistics.mean(head_ms),
+                              "median": statistics.median(head_ms), "best": min(head_ms),
+                              "worst": max(head_ms), "steps": len(head_ms),
+                              "note": "this rank's CUDA-event times of the timed steps"},
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
         "config": config_dict(args, head), "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clk, "roofline": roofline, "roofline_hbm": hbm_roof(head_kernel_ms),
