@@ -27,14 +27,15 @@ namespace sphx {
 constexpr int kTile = 128;  // arcs per tile = threads per block
 constexpr int kAdaptive = 5;
 
+// The integer-limb mode asks for 7 resident blocks per SM (72 registers, a
+// few bytes of spills): with its square root and reciprocal on the integer
+// pipe it is bound by instruction issue, and the extra warps hide more of the
+// carry chains' latency (1-1.5 % on GB300 against 6 blocks at 80 registers).
 template <int Mode>
-__global__ void __launch_bounds__(kTile) dense_kernel(const double *__restrict__ A,
-                                                      const double *__restrict__ B,
-                                                      const double *__restrict__ Z, int64_t n,
-                                                      double *__restrict__ out_pts,
-                                                      int32_t *__restrict__ out_count,
-                                                      unsigned long long *fallback,
-                                                      double gate) {
+__global__ void __launch_bounds__(kTile, Mode == kWideInt ? 7 : 1)
+    dense_kernel(const double *__restrict__ A, const double *__restrict__ B,
+                 const double *__restrict__ Z, int64_t n, double *__restrict__ out_pts,
+                 int32_t *__restrict__ out_count, unsigned long long *fallback, double gate) {
     __shared__ __align__(16) double sA[3 * kTile];
     __shared__ __align__(16) double sB[3 * kTile];
     __shared__ __align__(16) double sZ[kTile];
