@@ -48,11 +48,11 @@ BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
 # thread instructions per arc of dense_kernel<WIDE> (ncu smsp__inst_executed.sum x 32
 # / arcs on the 10^6-arc stress workload): the integer-limb method's work per arc
-INST_PER_ARC = {"wide": 2359}
+INST_PER_ARC = {"wide": 2351}
 # DRAM bytes (read + write) of one launch of the headline kernel over the 10^6
 # stress arcs, from the same ncu capture (writes still in L2 at kernel end are
 # not counted)
-TRAFFIC_PER_LAUNCH = {"wide": 56.054e6 + 8.227e6}
+TRAFFIC_PER_LAUNCH = {"wide": 58.238e6 + 9.188e6}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
