@@ -340,6 +340,25 @@ def test_host_buffer_call_equals_device_call(n, pinned):
             hC.fill_(-9)
 
 
+@pytest.mark.parametrize("pinned", ["all", "none"])
+def test_host_buffer_call_adaptive_mode(pinned):
+    """The adaptive mode through the host-buffer call (in place, and through the
+    staged copies) equals the device call bit for bit."""
+    A, B, z = W.mixed_chunk(3, size=50_001)
+    cnt_d, pts_d = run(A, B, z, "adaptive")
+    hA, hB, hz = (torch.from_numpy(np.ascontiguousarray(v)) for v in (A, B, z))
+    hP = torch.full((len(z), 2, 3), 5.0, dtype=torch.float64)
+    hC = torch.full((len(z),), -9, dtype=torch.int32)
+    if pinned == "all":
+        hA, hB, hz, hP, hC = (t.pin_memory() for t in (hA, hB, hz, hP, hC))
+    with sphx.Context(0) as ctx:
+        sphx.sphx_intersect_gca_constlat_host(ctx, hA, hB, hz, hP, hC, "adaptive")
+        sphx.sphx_host_join(ctx)
+        torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy(), cnt_d)
+    assert P.same_bits(hP.numpy(), pts_d)
+
+
 def test_host_buffer_calls_overlap_and_join():
     """Successive host-buffer calls on one context, different batches, one
     join at the end: every call's outputs are complete and correct."""
