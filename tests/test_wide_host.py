@@ -11,6 +11,10 @@ bounds the kernel's accuracy argument uses:
 Seeded random mantissas plus the edge cases of each routine: f = 1/2, f just
 below 1, mantissas next to the FP32 seed's rounding steps, odd and even
 exponents, cancellation in sums.
+
+The whole integer-limb pair evaluation is built for the host too (nvcc, host
+code only): on uniform, stress and 10^+-30-scaled arcs it gives the exact
+oracle's hit counts on unflagged arcs and its correctly rounded points.
 """
 import ctypes
 import os
@@ -24,6 +28,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "wide_host_harness.cpp")
 OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "wide_host_harness.so")
+PAIR_SRC = os.path.join(ROOT, "tests", "wide_host_pair.cu")
+PAIR_OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "wide_host_pair.so")
 TOP = 1 << 95
 
 
@@ -143,3 +149,47 @@ def test_conversion_to_double_rounds_to_nearest_even(lib):
         e, neg = rng.randrange(-100, 100), rng.randrange(2)
         got = lib.h_to_double(limbs(M), e, neg)
         assert F(got) == F(float(value(M, e, neg)))  # Python rounds a Fraction to nearest even
+
+
+@pytest.fixture(scope="module")
+def pair_lib():
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc"
+                                     if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("no nvcc for the host build of the pair evaluation")
+    os.makedirs(os.path.dirname(PAIR_OUT), exist_ok=True)
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", PAIR_OUT,
+                    PAIR_SRC], check=True)
+    L = ctypes.CDLL(PAIR_OUT)
+    L.h_pair_wide.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p,
+                                                       ctypes.c_void_p]
+    return L
+
+
+@pytest.mark.parametrize("gen", ["uniform", "stress", "scaled"])
+def test_pair_evaluation_on_the_host_matches_exact_oracle(pair_lib, gen):
+    import numpy as np
+    from oracle import exact
+    from paper_2510_09892_gb300 import workloads as W
+    if gen == "uniform":
+        A, B, z = W.uniform_arcs(2000, seed=91)
+    else:
+        A, B, z = W.stress_arcs(2000, seed=92)
+        if gen == "scaled":
+            rng = np.random.default_rng(93)
+            A = A * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+            B = B * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
+    n = len(z)
+    pts = np.empty((n, 2, 3))
+    cnt = np.empty(n, dtype=np.int32)
+    pair_lib.h_pair_wide(A.ctypes.data, B.ctypes.data, z.ctypes.data, n, pts.ctypes.data,
+                         cnt.ctypes.data)
+    ce, pe, fe = exact.intersect_batch(A, B, z, processes=1)
+    ok = fe == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(cnt[ok], ce[ok])
+    hit = np.isfinite(pe[..., 0]) & ok[:, None]
+    assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
+    # correctly rounded: the same doubles as the oracle on every unflagged hit
+    assert np.array_equal(pts[hit][:, :2], pe[hit][:, :2])
