@@ -163,6 +163,8 @@ def pair_lib():
     L = ctypes.CDLL(PAIR_OUT)
     L.h_pair_wide.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p,
                                                        ctypes.c_void_p]
+    L.h_arcs_wide.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p,
+                                                       ctypes.c_void_p]
     return L
 
 
@@ -193,3 +195,29 @@ def test_pair_evaluation_on_the_host_matches_exact_oracle(pair_lib, gen):
     assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
     # correctly rounded: the same doubles as the oracle on every unflagged hit
     assert np.array_equal(pts[hit][:, :2], pe[hit][:, :2])
+
+
+@pytest.mark.parametrize("scaled", [False, True])
+def test_arc_pairs_on_the_host_match_exact_oracle(pair_lib, scaled):
+    """Arc x arc in integer limbs, the same source built for the host: the exact
+    oracle's hit counts on unflagged pairs and its correctly rounded points."""
+    import numpy as np
+    from oracle import exact_arcs
+    from paper_2510_09892_gb300 import workloads as W
+    A1, A2, B1, B2 = W.arc_pairs(2000, seed=94)
+    if scaled:
+        sc = 10.0 ** np.random.default_rng(95).uniform(-30, 30, (4, len(A1), 1))
+        A1, A2, B1, B2 = A1 * sc[0], A2 * sc[1], B1 * sc[2], B2 * sc[3]
+    A1, A2, B1, B2 = (np.ascontiguousarray(v, dtype=np.float64) for v in (A1, A2, B1, B2))
+    n = len(A1)
+    pts = np.empty((n, 2, 3))
+    cnt = np.empty(n, dtype=np.int32)
+    pair_lib.h_arcs_wide(A1.ctypes.data, A2.ctypes.data, B1.ctypes.data, B2.ctypes.data, n,
+                         pts.ctypes.data, cnt.ctypes.data)
+    ce, pe, fe = exact_arcs.intersect_arcs_batch(A1, A2, B1, B2, processes=1)
+    ok = fe == 0
+    assert ok.mean() > 0.9
+    assert np.array_equal(cnt[ok], ce[ok])
+    hit = np.isfinite(pe[..., 0]) & ok[:, None]
+    assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
+    assert np.array_equal(pts[hit], pe[hit])

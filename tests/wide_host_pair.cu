@@ -1,8 +1,8 @@
-// Host build of the integer-limb pair evaluation (pair_wide in
-// paper_2510_09892_gb300/csrc/intersect.cuh is __host__ __device__), exported
-// for tests/test_wide_host.py: the same source as the GPU kernels, run on the
-// CPU against the exact oracle.
-#include "../paper_2510_09892_gb300/csrc/intersect.cuh"
+// Host builds of the integer-limb evaluations (pair_wide in
+// paper_2510_09892_gb300/csrc/intersect.cuh and arcs_wide in arcs.cuh are
+// __host__ __device__), exported for tests/test_wide_host.py: the same source
+// as the GPU kernels, run on the CPU against the exact oracles.
+#include "../paper_2510_09892_gb300/csrc/arcs.cuh"
 
 extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, long long n,
                             double *pts, int *cnt) {
@@ -18,5 +18,25 @@ extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, l
             pts[6 * i + 3 * r + 2] = o.hit[r] ? Z[i] : nan;
         }
         cnt[i] = o.count;
+    }
+}
+
+extern "C" void h_arcs_wide(const double *A1, const double *A2, const double *B1,
+                            const double *B2, long long n, double *pts, int *cnt) {
+    const double nan = __builtin_nan("");
+    for (long long i = 0; i < n; ++i) {
+        const double a1[3] = {A1[3 * i], A1[3 * i + 1], A1[3 * i + 2]};
+        const double a2[3] = {A2[3 * i], A2[3 * i + 1], A2[3 * i + 2]};
+        const double b1[3] = {B1[3 * i], B1[3 * i + 1], B1[3 * i + 2]};
+        const double b2[3] = {B2[3 * i], B2[3 * i + 1], B2[3 * i + 2]};
+        sphx::ArcOut r;
+        sphx::arcs_wide(a1, a2, b1, b2, r);
+        for (int k = 0; k < 2; ++k) {
+            const bool h = r.o.hit[k];
+            pts[6 * i + 3 * k + 0] = h ? r.o.px[k] : nan;
+            pts[6 * i + 3 * k + 1] = h ? r.o.py[k] : nan;
+            pts[6 * i + 3 * k + 2] = h ? (k == 0 ? r.pz : -r.pz) : nan;
+        }
+        cnt[i] = r.o.count;
     }
 }
