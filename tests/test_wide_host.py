@@ -165,6 +165,8 @@ def pair_lib():
                                                        ctypes.c_void_p]
     L.h_arcs_wide.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p,
                                                        ctypes.c_void_p]
+    L.h_pair_ff2.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p,
+                                                      ctypes.c_void_p]
     return L
 
 
@@ -221,3 +223,28 @@ def test_arc_pairs_on_the_host_match_exact_oracle(pair_lib, scaled):
     hit = np.isfinite(pe[..., 0]) & ok[:, None]
     assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
     assert np.array_equal(pts[hit], pe[hit])
+
+
+@pytest.mark.parametrize("gen", ["uniform", "stress"])
+def test_float_float_on_the_host_within_stated_bound(pair_lib, gen):
+    """The float-float form, the same source built for the host: every unflagged
+    hit within its stated bound; hit counts exact on uniform arcs, and off only
+    where s^2 is below float-float resolution on the stress mix (<= 3 %)."""
+    import numpy as np
+    from oracle import exact
+    from paper_2510_09892_gb300 import workloads as W
+    from tests import parity as P
+    A, B, z = W.uniform_arcs(2000, seed=96) if gen == "uniform" else W.stress_arcs(2000, seed=97)
+    A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
+    n = len(z)
+    pts = np.empty((n, 2, 3))
+    cnt = np.empty(n, dtype=np.int32)
+    pair_lib.h_pair_ff2(A.ctypes.data, B.ctypes.data, z.ctypes.data, n, pts.ctypes.data,
+                        cnt.ctypes.data)
+    ce, pe, fe = exact.intersect_batch(A, B, z, processes=1)
+    ok = fe == 0
+    hit = np.isfinite(pe[..., 0]) & np.isfinite(pts[..., 0]) & ok[:, None]
+    err = P.norm_error(pts, pe, z)
+    assert (np.where(hit, err, 0) <= P.ff_bound(A, B, z)[:, None]).all()
+    mism = (cnt != ce) & ok
+    assert mism.mean() <= (0.03 if gen == "stress" else 0.0)
