@@ -1,28 +1,54 @@
-// Device error-free transformations and compensated operators (Sec. 5 of
-// Chen, Ullrich, Panetta, arXiv 2510.09892), for FP64 and FP32.
+// Error-free transformations and compensated operators (Sec. 5 of Chen,
+// Ullrich, Panetta, arXiv 2510.09892), for FP64 and FP32.
 //
 // Every step is one correctly rounded IEEE operation written with an explicit
-// rounding intrinsic (__dadd_rn, __dmul_rn, __fma_rn, ...), so nvcc can never
-// contract a product and a sum into an FMA and change a rounding: the same
-// discipline the paper gets from -ffp-contract=off (Sec. 7.2).
+// rounding intrinsic on the device (__dadd_rn, __dmul_rn, __fma_rn, ...), so
+// nvcc can never contract a product and a sum into an FMA and change a
+// rounding: the same discipline the paper gets from -ffp-contract=off
+// (Sec. 7.2). The functions also build for the host (plain IEEE operations,
+// fma and sqrt, all correctly rounded; the host build of a caller must not
+// contract), so the kernels' source can be checked on the CPU.
 #pragma once
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define EFT_HD __host__ __device__ __forceinline__
+#else
+#define EFT_HD inline
+#endif
 
 namespace sphx {
 
 // ---- rounding-explicit scalar operations ------------------------------------
-__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+#if defined(__CUDA_ARCH__)
+EFT_HD double add(double a, double b) { return __dadd_rn(a, b); }
+EFT_HD double sub(double a, double b) { return __dsub_rn(a, b); }
+EFT_HD double mul(double a, double b) { return __dmul_rn(a, b); }
+EFT_HD double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+EFT_HD double div_(double a, double b) { return __ddiv_rn(a, b); }
+EFT_HD double sqrt_(double a) { return __dsqrt_rn(a); }
 
-__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float div_(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+EFT_HD float add(float a, float b) { return __fadd_rn(a, b); }
+EFT_HD float sub(float a, float b) { return __fsub_rn(a, b); }
+EFT_HD float mul(float a, float b) { return __fmul_rn(a, b); }
+EFT_HD float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+EFT_HD float div_(float a, float b) { return __fdiv_rn(a, b); }
+EFT_HD float sqrt_(float a) { return __fsqrt_rn(a); }
+#else
+EFT_HD double add(double a, double b) { return a + b; }
+EFT_HD double sub(double a, double b) { return a - b; }
+EFT_HD double mul(double a, double b) { return a * b; }
+EFT_HD double fma_(double a, double b, double c) { return ::fma(a, b, c); }
+EFT_HD double div_(double a, double b) { return a / b; }
+EFT_HD double sqrt_(double a) { return ::sqrt(a); }
+
+EFT_HD float add(float a, float b) { return a + b; }
+EFT_HD float sub(float a, float b) { return a - b; }
+EFT_HD float mul(float a, float b) { return a * b; }
+EFT_HD float fma_(float a, float b, float c) { return ::fmaf(a, b, c); }
+EFT_HD float div_(float a, float b) { return a / b; }
+EFT_HD float sqrt_(float a) { return ::sqrtf(a); }
+#endif
 
 template <typename T>
 struct Pair {  // unevaluated sum hi + lo
@@ -31,7 +57,7 @@ struct Pair {  // unevaluated sum hi + lo
 
 // TwoSum (Knuth): s = fl(a + b) and a + b = s + e exactly; no precondition.
 template <typename T>
-__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+EFT_HD void two_sum(T a, T b, T &s, T &e) {
     T x = add(a, b);
     T bv = sub(x, a);
     T av = sub(x, bv);
@@ -43,7 +69,7 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
 
 // FastTwoSum (Dekker): exact when exponent(a) >= exponent(b).
 template <typename T>
-__device__ __forceinline__ void fast_two_sum(T a, T b, T &s, T &e) {
+EFT_HD void fast_two_sum(T a, T b, T &s, T &e) {
     T x = add(a, b);
     T z = sub(x, a);
     s = x;
@@ -52,7 +78,7 @@ __device__ __forceinline__ void fast_two_sum(T a, T b, T &s, T &e) {
 
 // TwoProd with FMA: p = fl(a b) and a b = p + e exactly.
 template <typename T>
-__device__ __forceinline__ void two_prod(T a, T b, T &p, T &e) {
+EFT_HD void two_prod(T a, T b, T &p, T &e) {
     T x = mul(a, b);
     p = x;
     e = fma_(a, b, -x);
@@ -60,7 +86,7 @@ __device__ __forceinline__ void two_prod(T a, T b, T &p, T &e) {
 
 // Algorithm 1, CompDotC: x . y as the pair (p, s), n >= 1 terms.
 template <typename T, int N>
-__device__ __forceinline__ void comp_dot_c(const T (&x)[N], const T (&y)[N], T &p_out, T &s_out) {
+EFT_HD void comp_dot_c(const T (&x)[N], const T (&y)[N], T &p_out, T &s_out) {
     T p, s;
     two_prod(x[0], y[0], p, s);
 #pragma unroll
@@ -76,7 +102,7 @@ __device__ __forceinline__ void comp_dot_c(const T (&x)[N], const T (&y)[N], T &
 
 // Algorithm 2, CompDot: fl(p + s) of CompDotC.
 template <typename T, int N>
-__device__ __forceinline__ T comp_dot(const T (&x)[N], const T (&y)[N]) {
+EFT_HD T comp_dot(const T (&x)[N], const T (&y)[N]) {
     T p, s;
     comp_dot_c<T, N>(x, y, p, s);
     return add(p, s);
@@ -87,7 +113,7 @@ __device__ __forceinline__ T comp_dot(const T (&x)[N], const T (&y)[N]) {
 // would add the two product errors with the wrong sign. With renorm, one more
 // TwoSum makes |err| <= u |dop| (the pair's value is unchanged).
 template <typename T, bool Renorm>
-__device__ __forceinline__ void accu_dop(T a, T b, T c, T d, T &dop, T &err) {
+EFT_HD void accu_dop(T a, T b, T c, T d, T &dop, T &err) {
     T p1, r1, p2, r2, s;
     two_prod(a, d, p1, r1);
     two_prod(b, c, p2, r2);
@@ -98,7 +124,7 @@ __device__ __forceinline__ void accu_dop(T a, T b, T c, T d, T &dop, T &err) {
 
 // Algorithm 6, SumNonNeg: [A, a] + [B, b] for non-negative pairs.
 template <typename T>
-__device__ __forceinline__ void sum_non_neg(T A, T a, T B, T b, T &S, T &s) {
+EFT_HD void sum_non_neg(T A, T a, T B, T b, T &S, T &s) {
     T H, h;
     two_sum(A, B, H, h);
     T c = add(a, b);
@@ -108,7 +134,7 @@ __device__ __forceinline__ void sum_non_neg(T A, T a, T B, T b, T &S, T &s) {
 
 // Algorithm 5, SumOfSquares: |x|^2 as a pair (starting from the pair (0, 0)).
 template <typename T, int N>
-__device__ __forceinline__ void sum_of_squares(const T (&x)[N], T &S, T &s) {
+EFT_HD void sum_of_squares(const T (&x)[N], T &S, T &s) {
     T Sa = T(0), sa = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -122,7 +148,7 @@ __device__ __forceinline__ void sum_of_squares(const T (&x)[N], T &S, T &s) {
 
 // Algorithm 7, SumOfSquaresC: |x + e|^2 as a pair, dropping the e^2 terms.
 template <typename T, int N>
-__device__ __forceinline__ void sum_of_squares_c(const T (&x)[N], const T (&e)[N], T &S, T &s) {
+EFT_HD void sum_of_squares_c(const T (&x)[N], const T (&e)[N], T &S, T &s) {
     T Ss, ss;
     sum_of_squares<T, N>(x, Ss, ss);
     T Rs = comp_dot<T, N>(x, e);
@@ -136,7 +162,7 @@ __device__ __forceinline__ void sum_of_squares_c(const T (&x)[N], const T (&e)[N
 // by one FMA for a correctly rounded r, and the first-order Taylor term gives
 // er = (S - r^2 + e) / (2 r). S == 0 gives (0, 0).
 template <typename T>
-__device__ __forceinline__ void acc_sqrt(T S, T e, T &r_out, T &er_out) {
+EFT_HD void acc_sqrt(T S, T e, T &r_out, T &er_out) {
     if (S == T(0)) {
         r_out = T(0);
         er_out = T(0);

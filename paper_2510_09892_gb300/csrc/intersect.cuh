@@ -28,7 +28,7 @@ struct PairOut {
     double px[2], py[2];
 };
 
-__device__ __forceinline__ bool finite7(const double (&x1)[3], const double (&x2)[3], double z0) {
+EFT_HD bool finite7(const double (&x1)[3], const double (&x2)[3], double z0) {
     return isfinite(x1[0]) && isfinite(x1[1]) && isfinite(x1[2]) && isfinite(x2[0]) &&
            isfinite(x2[1]) && isfinite(x2[2]) && isfinite(z0);
 }
@@ -40,7 +40,7 @@ SPHX_HD void clear(PairOut &o, int count) {
 }
 
 // ---- Sec. 4: direct FP64 translation of Eq. 2.2 (no FMA anywhere) -----------
-__device__ __forceinline__ void pair_direct(const double (&x1)[3], const double (&x2)[3],
+EFT_HD void pair_direct(const double (&x1)[3], const double (&x2)[3],
                                             double z0, PairOut &o) {
     if (!finite7(x1, x2, z0)) return clear(o, 0);
     double nx = sub(mul(x1[1], x2[2]), mul(x1[2], x2[1]));
@@ -88,7 +88,7 @@ __device__ __forceinline__ void pair_direct(const double (&x1)[3], const double 
 // App. A, 16 doubles: n[3], en[3], S2, s2, S3, s3, ss, ess, sb, es, X (root
 // 0's x-coordinate numerator), 0 -- zeros past the point where the arc stops
 template <bool Renorm>
-__device__ __forceinline__ void pair_accux(const double (&x1)[3], const double (&x2)[3],
+EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
                                            double z0, PairOut &o, double *mid = nullptr) {
     if (mid) {
 #pragma unroll

@@ -12,9 +12,13 @@ Seeded random mantissas plus the edge cases of each routine: f = 1/2, f just
 below 1, mantissas next to the FP32 seed's rounding steps, odd and even
 exponents, cancellation in sums.
 
-The whole integer-limb pair evaluation is built for the host too (nvcc, host
-code only): on uniform, stress and 10^+-30-scaled arcs it gives the exact
-oracle's hit counts on unflagged arcs and its correctly rounded points.
+The kernels' per-pair evaluations are built for the host too (nvcc, host code
+only, no FMA contraction) and checked on the CPU:
+  * integer limbs (latitude and arc x arc): the exact oracle's hit counts on
+    unflagged arcs and its correctly rounded points, bit for bit;
+  * float-float: its stated bound;
+  * AccuX (renormalised and as printed) and direct FP64: the step-by-step FP64
+    reference, bit for bit.
 """
 import ctypes
 import os
@@ -158,15 +162,15 @@ def pair_lib():
     if nvcc is None:
         pytest.skip("no nvcc for the host build of the pair evaluation")
     os.makedirs(os.path.dirname(PAIR_OUT), exist_ok=True)
-    subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", PAIR_OUT,
-                    PAIR_SRC], check=True)
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-ffp-contract=off",
+                    "-o", PAIR_OUT, PAIR_SRC], check=True)
     L = ctypes.CDLL(PAIR_OUT)
     L.h_pair_wide.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p,
                                                        ctypes.c_void_p]
     L.h_arcs_wide.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_longlong, ctypes.c_void_p,
                                                        ctypes.c_void_p]
-    L.h_pair_ff2.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p,
-                                                      ctypes.c_void_p]
+    for f in (L.h_pair_ff2, L.h_pair_direct, L.h_pair_accux, L.h_pair_accux_printed):
+        f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
     return L
 
 
@@ -248,3 +252,29 @@ def test_float_float_on_the_host_within_stated_bound(pair_lib, gen):
     assert (np.where(hit, err, 0) <= P.ff_bound(A, B, z)[:, None]).all()
     mism = (cnt != ce) & ok
     assert mism.mean() <= (0.03 if gen == "stress" else 0.0)
+
+
+@pytest.mark.parametrize("form", ["accux", "accux_printed", "direct"])
+@pytest.mark.parametrize("gen", ["uniform", "stress"])
+def test_fp64_forms_on_the_host_equal_step_reference(pair_lib, form, gen):
+    """AccuX (renormalised and as printed) and direct FP64, the kernels' source
+    built for the host, equal the step-by-step FP64 reference bit for bit: the
+    same correctly rounded operations in the same order."""
+    import numpy as np
+    from oracle import steps
+    from paper_2510_09892_gb300 import workloads as W
+    from tests import parity as P
+    A, B, z = W.uniform_arcs(3000, seed=98) if gen == "uniform" else W.stress_arcs(3000, seed=99)
+    A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
+    n = len(z)
+    pts = np.empty((n, 2, 3))
+    cnt = np.empty(n, dtype=np.int32)
+    fn = {"accux": pair_lib.h_pair_accux, "accux_printed": pair_lib.h_pair_accux_printed,
+          "direct": pair_lib.h_pair_direct}[form]
+    fn(A.ctypes.data, B.ctypes.data, z.ctypes.data, n, pts.ctypes.data, cnt.ctypes.data)
+    if form == "direct":
+        cr, pr = steps.direct(A, B, z)
+    else:
+        cr, pr = steps.accux(A, B, z, variant=2 if form == "accux" else 0)
+    assert np.array_equal(cnt, cr)
+    assert P.same_bits(pts, pr)

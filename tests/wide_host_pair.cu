@@ -1,7 +1,8 @@
-// Host builds of the evaluations written for host and device (pair_wide and
-// pair_ff2 in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
-// arcs.cuh), exported for tests/test_wide_host.py: the same source as the GPU
-// kernels, run on the CPU against the exact oracles.
+// Host builds of the per-pair evaluations (pair_wide, pair_ff2, pair_accux and
+// pair_direct in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
+// arcs.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
+// same source as the GPU kernels, run on the CPU against the exact oracles and
+// the step-by-step FP64 reference. Built with FMA contraction off.
 #include "../paper_2510_09892_gb300/csrc/arcs.cuh"
 
 extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, long long n,
@@ -19,6 +20,44 @@ extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, l
         }
         cnt[i] = o.count;
     }
+}
+
+template <int Which>
+static void run_fp64(const double *A, const double *B, const double *Z, long long n,
+                     double *pts, int *cnt) {
+    const double nan = __builtin_nan("");
+    for (long long i = 0; i < n; ++i) {
+        const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
+        const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        sphx::PairOut o;
+        if (Which == 0)
+            sphx::pair_direct(x1, x2, Z[i], o);
+        else if (Which == 1)
+            sphx::pair_accux<true>(x1, x2, Z[i], o);
+        else
+            sphx::pair_accux<false>(x1, x2, Z[i], o);
+        for (int r = 0; r < 2; ++r) {
+            pts[6 * i + 3 * r + 0] = o.hit[r] ? o.px[r] : nan;
+            pts[6 * i + 3 * r + 1] = o.hit[r] ? o.py[r] : nan;
+            pts[6 * i + 3 * r + 2] = o.hit[r] ? Z[i] : nan;
+        }
+        cnt[i] = o.count;
+    }
+}
+
+extern "C" void h_pair_direct(const double *A, const double *B, const double *Z, long long n,
+                              double *pts, int *cnt) {
+    run_fp64<0>(A, B, Z, n, pts, cnt);
+}
+
+extern "C" void h_pair_accux(const double *A, const double *B, const double *Z, long long n,
+                             double *pts, int *cnt) {
+    run_fp64<1>(A, B, Z, n, pts, cnt);
+}
+
+extern "C" void h_pair_accux_printed(const double *A, const double *B, const double *Z,
+                                     long long n, double *pts, int *cnt) {
+    run_fp64<2>(A, B, Z, n, pts, cnt);
 }
 
 extern "C" void h_pair_ff2(const double *A, const double *B, const double *Z, long long n,
