@@ -45,13 +45,13 @@ constexpr double kEta = 4.9406564584124654e-324;  // 2^-1074
 constexpr double kSafe = 1.0 + 9.094947017729282e-13;  // 1 + 2^-40
 
 // ulp of a positive double: 2^(exponent - 52), never below 2^-1074
-__device__ __forceinline__ double ulp_pos(double x) {
+EFT_HD double ulp_pos(double x) {
     const uint64_t e = (wide::bits_of(x) >> 52) & 0x7ff;
     return e > 52 ? wide::double_of((e - 52) << 52) : kEta;
 }
 
 // the accepted range of input magnitudes
-__device__ __forceinline__ bool in_range(double v) {
+EFT_HD bool in_range(double v) {
     const double a = fabs(v);
     return a == 0.0 || (a >= 7.888609052210118e-31 && a <= 1.2676506002282294e30);  // 2^-100, 2^100
 }
@@ -62,7 +62,7 @@ __device__ __forceinline__ bool in_range(double v) {
 // value; small ones on G u rho. rho~ has a relative error below 3u, so
 // 0.975 G u rho~ < G u rho, and the class boundary 2^-20 rho is tested with a
 // 2^-40 margin on either side. gate = 0.975 G.
-__device__ __forceinline__ bool within_gate(double p, double B, double rho, double gate) {
+EFT_HD bool within_gate(double p, double B, double rho, double gate) {
     const double a = fabs(p);
     const double thr = 9.5367431640625e-07 * rho;  // 2^-20 rho
     const double lo = (a - B) * (1.0 - 8.881784197001252e-16);  // below a - B (1 - 2^-50)
@@ -77,7 +77,7 @@ __device__ __forceinline__ bool within_gate(double p, double B, double rho, doub
 // conventions as the other modes) when the bound vouches for the result
 // within gate / 0.975 ulp per component, false when the lane must be
 // re-evaluated.
-__device__ __forceinline__ bool pair_filtered(const double (&x1)[3], const double (&x2)[3],
+EFT_HD bool pair_filtered(const double (&x1)[3], const double (&x2)[3],
                                               double z0, double gate, PairOut &o) {
     if (!(in_range(x1[0]) && in_range(x1[1]) && in_range(x1[2]) && in_range(x2[0]) &&
           in_range(x2[1]) && in_range(x2[2]) && in_range(z0)))

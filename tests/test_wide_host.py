@@ -18,7 +18,9 @@ only, no FMA contraction) and checked on the CPU:
     unflagged arcs and its correctly rounded points, bit for bit;
   * float-float: its stated bound;
   * AccuX (renormalised and as printed) and direct FP64: the step-by-step FP64
-    reference, bit for bit.
+    reference, bit for bit;
+  * the adaptive filter's error bound: every arc it keeps has the exact hit
+    count (near-boundary arcs included) and points within the gate.
 """
 import ctypes
 import os
@@ -171,6 +173,9 @@ def pair_lib():
                                                        ctypes.c_void_p]
     for f in (L.h_pair_ff2, L.h_pair_direct, L.h_pair_accux, L.h_pair_accux_printed):
         f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]
+    L.h_pair_filtered.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_double,
+                                                          ctypes.c_void_p, ctypes.c_void_p,
+                                                          ctypes.c_void_p]
     return L
 
 
@@ -278,3 +283,42 @@ def test_fp64_forms_on_the_host_equal_step_reference(pair_lib, form, gen):
         cr, pr = steps.accux(A, B, z, variant=2 if form == "accux" else 0)
     assert np.array_equal(cnt, cr)
     assert P.same_bits(pts, pr)
+
+
+@pytest.mark.parametrize("gen,gate,min_kept", [("uniform", 4.0, 0.0), ("uniform", 64.0, 0.3),
+                                               ("stress", 2.0 ** 20, 0.08),
+                                               ("scaled", 2.0 ** 20, 0.0)])
+def test_adaptive_filter_bound_on_the_host(pair_lib, gen, gate, min_kept):
+    """The adaptive filter's running error bound, the kernel's source built for
+    the host: every arc it keeps has the exact oracle's hit count (flagged arcs
+    included) and points within the gate."""
+    import numpy as np
+    from oracle import exact
+    from paper_2510_09892_gb300 import workloads as W
+    from tests import parity as P
+    if gen == "uniform":
+        A, B, z = W.uniform_arcs(3000, seed=100)
+    else:
+        A, B, z = W.stress_arcs(3000, seed=101)
+        if gen == "scaled":
+            rng = np.random.default_rng(102)
+            A = A * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+            B = B * (10.0 ** rng.uniform(-30, 30, len(z)))[:, None]
+    A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
+    n = len(z)
+    pts = np.empty((n, 2, 3))
+    cnt = np.empty(n, dtype=np.int32)
+    kept = np.empty(n, dtype=np.int32)
+    pair_lib.h_pair_filtered(A.ctypes.data, B.ctypes.data, z.ctypes.data, n, gate,
+                             pts.ctypes.data, cnt.ctypes.data, kept.ctypes.data)
+    k = kept == 1
+    print(f"{gen}, gate {gate:g}: kept {k.mean():.3f}")
+    assert k.mean() >= min_kept
+    if not k.any():
+        return
+    ce, pe, fe = exact.intersect_batch(A[k], B[k], z[k], processes=1)
+    assert np.array_equal(cnt[k], ce)
+    hit = np.isfinite(pe[..., 0])
+    assert np.array_equal(np.isfinite(pts[k][..., 0]), hit)
+    _, _, g = P.component_errors(pts[k], pe, z[k])
+    assert np.nanmax(np.where(hit[..., None], g, 0.0), initial=0.0) <= gate

@@ -1,8 +1,9 @@
 // Host builds of the per-pair evaluations (pair_wide, pair_ff2, pair_accux and
 // pair_direct in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
-// arcs.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
+// arcs.cuh and the adaptive filter in adaptive.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
 // same source as the GPU kernels, run on the CPU against the exact oracles and
 // the step-by-step FP64 reference. Built with FMA contraction off.
+#include "../paper_2510_09892_gb300/csrc/adaptive.cuh"
 #include "../paper_2510_09892_gb300/csrc/arcs.cuh"
 
 extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, long long n,
@@ -94,5 +95,25 @@ extern "C" void h_arcs_wide(const double *A1, const double *A2, const double *B1
             pts[6 * i + 3 * k + 2] = h ? (k == 0 ? r.pz : -r.pz) : nan;
         }
         cnt[i] = r.o.count;
+    }
+}
+
+// the adaptive filter alone: kept[i] = 1 where it vouches for arc i (its
+// result in pts and cnt), 0 where the kernel would hand the arc on
+extern "C" void h_pair_filtered(const double *A, const double *B, const double *Z, long long n,
+                                double gate_ulps, double *pts, int *cnt, int *kept) {
+    const double nan = __builtin_nan("");
+    for (long long i = 0; i < n; ++i) {
+        const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
+        const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        sphx::PairOut o;
+        kept[i] = sphx::filt::pair_filtered(x1, x2, Z[i], 0.975 * gate_ulps, o) ? 1 : 0;
+        for (int r = 0; r < 2; ++r) {
+            const bool h = kept[i] && o.hit[r];
+            pts[6 * i + 3 * r + 0] = h ? o.px[r] : nan;
+            pts[6 * i + 3 * r + 1] = h ? o.py[r] : nan;
+            pts[6 * i + 3 * r + 2] = h ? Z[i] : nan;
+        }
+        cnt[i] = kept[i] ? o.count : -9;
     }
 }
