@@ -441,8 +441,7 @@ SPHX_HD void pair_ff2(const double (&x1)[3], const double (&x2)[3], double z0, P
 }
 
 template <int Mode>
-__device__ __forceinline__ void intersect_pair(const double (&x1)[3], const double (&x2)[3],
-                                               double z0, PairOut &o) {
+EFT_HD void intersect_pair(const double (&x1)[3], const double (&x2)[3], double z0, PairOut &o) {
     if (Mode == kDirect)
         pair_direct(x1, x2, z0, o);
     else if (Mode == kEftFp64)

@@ -6,9 +6,35 @@
 
 namespace sphx {
 
+// three device intrinsics with host equivalents, so that the functions below
+// also build for the host (tests); the device code is unchanged
+EFT_HD double rsqrt_hd(double x) {
+#if defined(__CUDA_ARCH__)
+    return rsqrt(x);
+#else
+    return 1.0 / sqrt(x);
+#endif
+}
+
+EFT_HD float rsqrtf_hd(float x) {
+#if defined(__CUDA_ARCH__)
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+
+EFT_HD int hi_word(double v) {
+#if defined(__CUDA_ARCH__)
+    return __double2hiint(v);
+#else
+    return (int)(wide::bits_of(v) >> 32);
+#endif
+}
+
 // first index i in [0, n) with a[i] > key (n if none)
 template <typename T>
-__device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t n, T key) {
+EFT_HD int64_t upper_bound_dev(const T *a, int64_t n, T key) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -23,13 +49,13 @@ __device__ __forceinline__ int64_t upper_bound_dev(const T *a, int64_t n, T key)
 // images compares the values, with no FP64 instruction (GB300 issues FP64
 // comparisons at 2 per SM per clock, 64-bit integer ones far faster).
 // -0.0 maps just below +0.0, which only matters for keys that widen a range.
-__device__ __forceinline__ long long ord64(double x) {
+EFT_HD long long ord64(double x) {
     const long long b = (long long)wide::bits_of(x);
     return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
 }
 
 // first index i in [0, n) with a[i] >= key (by ord64)
-__device__ __forceinline__ int64_t lower_bound_ord(const double *a, int64_t n, long long key) {
+EFT_HD int64_t lower_bound_ord(const double *a, int64_t n, long long key) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -42,7 +68,7 @@ __device__ __forceinline__ int64_t lower_bound_ord(const double *a, int64_t n, l
 }
 
 // first index i in [0, n) with a[i] > key (by ord64)
-__device__ __forceinline__ int64_t upper_bound_ord(const double *a, int64_t n, long long key) {
+EFT_HD int64_t upper_bound_ord(const double *a, int64_t n, long long key) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
@@ -58,8 +84,8 @@ __device__ __forceinline__ int64_t upper_bound_ord(const double *a, int64_t n, l
 // forward from `from` (steps 1, 2, 4, ... then a binary search): a few loads
 // when the answer is near `from`, as for the short ranges of latitudes an arc
 // spans
-__device__ __forceinline__ int64_t upper_bound_ord_from(const double *a, int64_t n, int64_t from,
-                                                        long long key) {
+EFT_HD int64_t upper_bound_ord_from(const double *a, int64_t n, int64_t from,
+                                    long long key) {
     int64_t lo = from, hi = from, step = 1;
     while (hi < n && ord64(a[hi]) <= key) {
         lo = hi + 1;
@@ -78,7 +104,7 @@ __device__ __forceinline__ int64_t upper_bound_ord_from(const double *a, int64_t
 }
 
 // a float in [-2, 2] as a double, by its bits (values below 2^-126 become +-0)
-__device__ __forceinline__ double f64_of_f32_small(float f) {
+EFT_HD double f64_of_f32_small(float f) {
     const uint32_t b = wide::fbits_of(f);
     const uint32_t fe = (b >> 23) & 0xffu;
     const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
@@ -90,8 +116,8 @@ __device__ __forceinline__ double f64_of_f32_small(float f) {
 constexpr double kZWiden = 1e-13;
 
 // binary exponent of |v| for a finite nonzero double (floor(log2 |v|))
-__device__ __forceinline__ int exponent_of(double v) {
-    int hi = __double2hiint(v);
+EFT_HD int exponent_of(double v) {
+    int hi = hi_word(v);
     int ex = (hi >> 20) & 0x7ff;
     if (ex == 0) return ilogb(v);  // subnormal
     return ex - 1023;
@@ -100,15 +126,15 @@ __device__ __forceinline__ int exponent_of(double v) {
 // z-range of the minor arc x1 -> x2 in FP64: the endpoints' z and, when the
 // arc passes it, the great circle's highest (or lowest) point +-|n_xy| / |n|,
 // widened by 1e-13; false for a degenerate or non-finite arc
-__device__ __forceinline__ bool z_range_fp64(const double (&x1)[3], const double (&x2)[3],
-                                             double &zmin, double &zmax) {
+EFT_HD bool z_range_fp64(const double (&x1)[3], const double (&x2)[3],
+                         double &zmin, double &zmax) {
     double n[3], en[3];
     accu_dop<double, true>(x1[1], x1[2], x2[1], x2[2], n[0], en[0]);
     accu_dop<double, true>(x1[2], x1[0], x2[2], x2[0], n[1], en[1]);
     accu_dop<double, true>(x1[0], x1[1], x2[0], x2[1], n[2], en[2]);
     if (!finite7(x1, x2, 0.0) || (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0)) return false;
-    const double z1 = x1[2] * rsqrt(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
-    const double z2 = x2[2] * rsqrt(x2[0] * x2[0] + x2[1] * x2[1] + x2[2] * x2[2]);
+    const double z1 = x1[2] * rsqrt_hd(x1[0] * x1[0] + x1[1] * x1[1] + x1[2] * x1[2]);
+    const double z2 = x2[2] * rsqrt_hd(x2[0] * x2[0] + x2[1] * x2[1] + x2[2] * x2[2]);
     zmin = fmin(z1, z2);
     zmax = fmax(z1, z2);
     // scale n to avoid underflow in the squares of very short arcs
@@ -156,8 +182,8 @@ constexpr float kZWiden32 = 1.0f / (1 << 19);
 // apex test and no FP64 difference are needed.
 constexpr float kShortChord2 = 1.0f / (1 << 18);
 
-__device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
-                                             double &zmin, double &zmax) {
+EFT_HD bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
+                         double &zmin, double &zmax) {
     float p1[3], p2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -170,7 +196,7 @@ __device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double
     {
         const float dx = p2[0] - p1[0], dy = p2[1] - p1[1], dz = p2[2] - p1[2];
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= kShortChord2) {
-            const float z1 = p1[2] * rsqrtf(q1), z2 = p2[2] * rsqrtf(q2);
+            const float z1 = p1[2] * rsqrtf_hd(q1), z2 = p2[2] * rsqrtf_hd(q2);
             zmin = f64_of_f32_small(fminf(z1, z2) - kZWiden32);
             zmax = f64_of_f32_small(fmaxf(z1, z2) + kZWiden32);
             return true;
@@ -185,7 +211,7 @@ __device__ __forceinline__ bool z_range_fp32(const double (&x1)[3], const double
     const float nz = fmaf(p1[0], d[1], -p1[1] * d[0]);
     const float S2 = fmaf(nx, nx, ny * ny), S3 = fmaf(nz, nz, S2);
     if (!(S3 > 1e-30f)) return false;
-    const float z1 = p1[2] * rsqrtf(q1), z2 = p2[2] * rsqrtf(q2);
+    const float z1 = p1[2] * rsqrtf_hd(q1), z2 = p2[2] * rsqrtf_hd(q2);
     float lo = fminf(z1, z2), hi = fmaxf(z1, z2);
     const float ax = -nx * nz, ay = -ny * nz, az = S2;
     const float m1x = fmaf(ny, p1[2], -nz * p1[1]), m1y = fmaf(nz, p1[0], -nx * p1[2]),

@@ -20,7 +20,9 @@ only, no FMA contraction) and checked on the CPU:
   * AccuX (renormalised and as printed) and direct FP64: the step-by-step FP64
     reference, bit for bit;
   * the adaptive filter's error bound: every arc it keeps has the exact hit
-    count (near-boundary arcs included) and points within the gate.
+    count (near-boundary arcs included) and points within the gate;
+  * the band-area routines (boundary integral, fan, fan plus sliver): the
+    band-area oracle within 32 u (longitude perimeter + height range).
 """
 import ctypes
 import os
@@ -176,6 +178,11 @@ def pair_lib():
     L.h_pair_filtered.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_longlong, ctypes.c_double,
                                                           ctypes.c_void_p, ctypes.c_void_p,
                                                           ctypes.c_void_p]
+    vp, ll = ctypes.c_void_p, ctypes.c_longlong
+    L.h_green_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp]
+    L.h_green_cells.restype = ctypes.c_uint
+    L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
+    L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
     return L
 
 
@@ -322,3 +329,66 @@ def test_adaptive_filter_bound_on_the_host(pair_lib, gen, gate, min_kept):
     assert np.array_equal(np.isfinite(pts[k][..., 0]), hit)
     _, _, g = P.component_errors(pts[k], pe, z[k])
     assert np.nanmax(np.where(hit[..., None], g, 0.0), initial=0.0) <= gate
+
+
+def _area_tolerance(cells):
+    """32 u (sum of |longitude steps| between nodes off the poles + height range)."""
+    import numpy as np
+    from oracle import areas as OA
+    out = []
+    for c in cells:
+        v = np.asarray(c)
+        zr = np.ptp(OA.breakpoints(c))
+        v = v[np.hypot(v[:, 0], v[:, 1]) > 0]
+        w = np.roll(v, -1, axis=0)
+        d = np.arctan2(v[:, 0] * w[:, 1] - v[:, 1] * w[:, 0], v[:, 0] * w[:, 0] + v[:, 1] * w[:, 1])
+        out.append(np.abs(d).sum() + zr)
+    return 32.0 * 2.0 ** -53 * np.array(out)
+
+
+@pytest.mark.parametrize("kind", ["polygons", "cubed_sphere"])
+def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
+    """The boundary integral on every cell; the fan on the cells the oracle puts
+    inside one interior band; the fan plus sliver on the cells it puts in two."""
+    import numpy as np
+    from oracle import areas as OA
+    from paper_2510_09892_gb300 import workloads as W
+    if kind == "polygons":
+        nodes, off, fn = W.polygon_cells(48, seed=33, radius=(1e-3, 0.4))
+        lat = W.latlon_latitudes(61)
+    else:  # odd N: the poles lie inside cells; 30-degree bands, so that cells
+        # of about 18 degrees lie in one or two of them
+        nodes, off, fn = W.cubed_sphere_cells(5)
+        lat = W.latlon_latitudes(7)
+    nodes, off, fn, lat = (np.ascontiguousarray(v) for v in (nodes, off.astype(np.int64),
+                                                              fn.astype(np.int32), lat))
+    cells = W.cells_as_lists(nodes, off, fn)
+    F, nb = len(off) - 1, len(lat) - 1
+    ref = np.array(OA.band_areas_batch(cells, lat, processes=min(8, os.cpu_count() or 1)))
+    tol = _area_tolerance(cells)
+    args = (nodes.ctypes.data, len(nodes), off.ctypes.data, fn.ctypes.data, F)
+    green = np.zeros((F, nb))
+    st = pair_lib.h_green_cells(*args, lat.ctypes.data, len(lat), green.ctypes.data)
+    assert st == 0
+    assert (np.abs(green - ref) <= tol[:, None]).all(), (np.abs(green - ref) / tol[:, None]).max()
+    # cells in one / two interior bands (by the oracle)
+    inside = ref > tol[:, None]
+    first = np.argmax(inside, axis=1)
+    nbands = inside.sum(axis=1)
+    interior = (first > 0) & (first + nbands < nb)
+    one = np.flatnonzero((nbands == 1) & interior)
+    two = np.flatnonzero((nbands == 2) & interior & inside[np.arange(F), np.minimum(first + 1, nb - 1)])
+    fan = np.empty(F)
+    pair_lib.h_fan_cells(*args, fan.ctypes.data)
+    done = one[np.isfinite(fan[one])]
+    assert len(one) > 0 and len(done) >= 0.5 * len(one)
+    assert (np.abs(fan[done] - ref[done].sum(axis=1)) <= tol[done]).all()
+    lo = first.astype(np.int32)
+    pr = np.empty(2 * F)
+    pair_lib.h_pair_cells(*args, lat.ctypes.data, len(lat), lo.ctypes.data, pr.ctypes.data)
+    pr = pr.reshape(F, 2)
+    done2 = two[np.isfinite(pr[two, 0])]
+    assert len(two) > 0 and len(done2) >= 0.5 * len(two)
+    want = np.stack([ref[done2, first[done2]], ref[done2, first[done2] + 1]], axis=1)
+    assert (np.abs(pr[done2] - want) <= tol[done2, None]).all()
+    print(f"{kind}: {F} cells, fan {len(done)}/{len(one)}, fan plus sliver {len(done2)}/{len(two)}")

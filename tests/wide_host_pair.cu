@@ -1,9 +1,11 @@
 // Host builds of the per-pair evaluations (pair_wide, pair_ff2, pair_accux and
 // pair_direct in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
-// arcs.cuh and the adaptive filter in adaptive.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
+// arcs.cuh, the adaptive filter in adaptive.cuh and the per-cell band-area
+// routines in areas.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
 // same source as the GPU kernels, run on the CPU against the exact oracles and
 // the step-by-step FP64 reference. Built with FMA contraction off.
 #include "../paper_2510_09892_gb300/csrc/adaptive.cuh"
+#include "../paper_2510_09892_gb300/csrc/areas.cuh"
 #include "../paper_2510_09892_gb300/csrc/arcs.cuh"
 
 extern "C" void h_pair_wide(const double *A, const double *B, const double *Z, long long n,
@@ -116,4 +118,69 @@ extern "C" void h_pair_filtered(const double *A, const double *B, const double *
         }
         cnt[i] = kept[i] ? o.count : -9;
     }
+}
+
+// band areas of every cell with the boundary integral (green_cell, crossings
+// in integer limbs), each cell given the full band range: out is n_faces x
+// (L - 1), row f the areas of cell f in bands 0 .. L - 2
+extern "C" unsigned h_green_cells(const double *nodes, long long n_nodes,
+                                  const long long *face_offsets, const int *face_nodes,
+                                  long long n_faces, const double *lat, long long L,
+                                  double *out) {
+    unsigned status = 0u;
+    sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
+                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status};
+    const long long nb = L - 1;
+    int32_t *lo = new int32_t[n_faces], *hi = new int32_t[n_faces];
+    long long *off = new long long[n_faces];
+    double *rho = new double[L];
+    for (long long k = 0; k < L; ++k) rho[k] = sphx::rho_of_lat(lat[k]);
+    for (long long f = 0; f < n_faces; ++f) {
+        lo[f] = 0;
+        hi[f] = (int32_t)nb;
+        off[f] = f * nb;
+    }
+    for (long long f = 0; f < n_faces; ++f)
+        sphx::green_cell<sphx::kWideInt>(m, f, lo, hi, off, out, n_faces * nb, lat, rho);
+    delete[] lo;
+    delete[] hi;
+    delete[] off;
+    delete[] rho;
+    return status;
+}
+
+// the fan area of every cell (fan_area): area[f], or NaN where the routine
+// declines the cell (a node more than 60 degrees from node 0)
+extern "C" void h_fan_cells(const double *nodes, long long n_nodes, const long long *face_offsets,
+                            const int *face_nodes, long long n_faces, double *area) {
+    unsigned status = 0u;
+    sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
+                 (int64_t)face_offsets[n_faces], n_faces, nullptr, 0, &status};
+    long long *off = new long long[n_faces];
+    for (long long f = 0; f < n_faces; ++f) {
+        off[f] = f;
+        area[f] = __builtin_nan("");
+    }
+    for (long long f = 0; f < n_faces; ++f) sphx::fan_area(m, f, off, area, n_faces);
+    delete[] off;
+}
+
+// the two band areas of each cell cut by the latitude lat[band_lo[f] + 1]
+// (pair_area, crossings in integer limbs): out[2 f], out[2 f + 1] for bands
+// band_lo[f] and band_lo[f] + 1, NaN where the routine declines the cell
+extern "C" void h_pair_cells(const double *nodes, long long n_nodes,
+                             const long long *face_offsets, const int *face_nodes,
+                             long long n_faces, const double *lat, long long L,
+                             const int *band_lo, double *out) {
+    unsigned status = 0u;
+    sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
+                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status};
+    long long *off = new long long[n_faces];
+    for (long long f = 0; f < n_faces; ++f) {
+        off[f] = 2 * f;
+        out[2 * f] = out[2 * f + 1] = __builtin_nan("");
+    }
+    for (long long f = 0; f < n_faces; ++f)
+        sphx::pair_area<sphx::kWideInt>(m, f, band_lo, off, out, 2 * n_faces, lat);
+    delete[] off;
 }
