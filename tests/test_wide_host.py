@@ -22,7 +22,10 @@ only, no FMA contraction) and checked on the CPU:
   * the adaptive filter's error bound: every arc it keeps has the exact hit
     count (near-boundary arcs included) and points within the gate;
   * the band-area routines (boundary integral, fan, fan plus sliver): the
-    band-area oracle within 32 u (longitude perimeter + height range).
+    band-area oracle within 32 u (longitude perimeter + height range);
+  * the height range of each arc that decides its candidate latitudes: it
+    contains the arc's exact height extent (so no hit is lost) and is widened
+    by no more than the FP32 margin.
 """
 import ctypes
 import os
@@ -183,6 +186,7 @@ def pair_lib():
     L.h_green_cells.restype = ctypes.c_uint
     L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
     L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
+    L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp]
     return L
 
 
@@ -392,3 +396,37 @@ def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
     want = np.stack([ref[done2, first[done2]], ref[done2, first[done2] + 1]], axis=1)
     assert (np.abs(pr[done2] - want) <= tol[done2, None]).all()
     print(f"{kind}: {F} cells, fan {len(done)}/{len(one)}, fan plus sliver {len(done2)}/{len(two)}")
+
+
+@pytest.mark.parametrize("gen", ["uniform", "stress", "scaled", "cubed_sphere", "meshes"])
+def test_candidate_height_ranges_contain_the_arcs(pair_lib, gen):
+    import numpy as np
+    from oracle import areas as OA
+    from paper_2510_09892_gb300 import workloads as W
+    if gen == "uniform":
+        A, B, _ = W.uniform_arcs(3000, seed=103)
+    elif gen in ("stress", "scaled"):
+        A, B, _ = W.stress_arcs(3000, seed=104)
+        if gen == "scaled":
+            rng = np.random.default_rng(105)
+            A = A * (10.0 ** rng.uniform(-30, 30, len(A)))[:, None]
+            B = B * (10.0 ** rng.uniform(-30, 30, len(B)))[:, None]
+    elif gen == "cubed_sphere":
+        A, B = W.cubed_sphere_edges(16)
+    else:
+        b = W.ragged_meshes(4, 40, 400, seed=106, lat_min=180, lat_max=300)
+        A, B = b["A"], b["B"]
+    A, B = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B))
+    n = len(A)
+    zmin, zmax = np.empty(n), np.empty(n)
+    ok = np.empty(n, dtype=np.int32)
+    pair_lib.h_z_ranges(A.ctypes.data, B.ctypes.data, n, zmin.ctypes.data, zmax.ctypes.data,
+                        ok.ctypes.data)
+    assert ok.all()
+    lo = np.empty(n)
+    hi = np.empty(n)
+    for i in range(n):
+        zs = OA.breakpoints([tuple(A[i]), tuple(B[i])])
+        lo[i], hi[i] = min(zs), max(zs)
+    assert (zmin <= lo).all() and (zmax >= hi).all()
+    assert ((zmax - zmin) - (hi - lo) <= 8 * 2.0 ** -19).all()

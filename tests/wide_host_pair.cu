@@ -184,3 +184,17 @@ extern "C" void h_pair_cells(const double *nodes, long long n_nodes,
         sphx::pair_area<sphx::kWideInt>(m, f, band_lo, off, out, 2 * n_faces, lat);
     delete[] off;
 }
+
+// the candidate kernel's height range of each arc (z_range_fp32, else
+// z_range_fp64, as in ragged.cu); ok[i] = 0 where neither gives one
+extern "C" void h_z_ranges(const double *A, const double *B, long long n, double *zmin,
+                           double *zmax, int *ok) {
+    for (long long i = 0; i < n; ++i) {
+        const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
+        const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        double lo = 0.0, hi = 0.0;
+        ok[i] = (sphx::z_range_fp32(x1, x2, lo, hi) || sphx::z_range_fp64(x1, x2, lo, hi)) ? 1 : 0;
+        zmin[i] = lo;
+        zmax[i] = hi;
+    }
+}
