@@ -187,6 +187,7 @@ def pair_lib():
     L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
     L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
     L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp]
+    L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     return L
 
 
@@ -430,3 +431,35 @@ def test_candidate_height_ranges_contain_the_arcs(pair_lib, gen):
         lo[i], hi[i] = min(zs), max(zs)
     assert (zmin <= lo).all() and (zmax >= hi).all()
     assert ((zmax - zmin) - (hi - lo) <= 8 * 2.0 ** -19).all()
+
+
+def test_latitude_searches_on_the_host(pair_lib):
+    """The order-preserving integer image of the doubles gives the same search
+    results as comparing the values (numpy.searchsorted), on latitude grids,
+    random sorted arrays with repeats, and keys on, between and outside the
+    values; -0.0 sorts just below +0.0."""
+    import numpy as np
+    from paper_2510_09892_gb300 import workloads as W
+    rng = np.random.default_rng(107)
+    arrays = [W.latlon_latitudes(721), W.latlon_latitudes(180),
+              np.sort(rng.uniform(-1, 1, 257)),
+              np.sort(np.round(rng.uniform(-1, 1, 300), 2)),  # repeats
+              np.array([0.5]), np.array([], dtype=np.float64)]
+    for a in arrays:
+        a = np.ascontiguousarray(a[a != 0.0] if len(a) else a, dtype=np.float64)
+        keys = np.concatenate([a, rng.uniform(-1.2, 1.2, 500), np.nextafter(a, 2), np.nextafter(a, -2),
+                               [-1.0, 1.0, 0.0, -0.0, np.inf, -np.inf]]).astype(np.float64)
+        m = len(keys)
+        lower, upper, gallop = (np.empty(m, dtype=np.int64) for _ in range(3))
+        pair_lib.h_searches(a.ctypes.data, len(a), keys.ctypes.data, m, lower.ctypes.data,
+                            upper.ctypes.data, gallop.ctypes.data)
+        assert np.array_equal(lower, np.searchsorted(a, keys, side="left"))
+        assert np.array_equal(upper, np.searchsorted(a, keys, side="right"))
+        assert np.array_equal(gallop, upper)
+    # signed zeros: -0.0 < +0.0 in the image
+    a = np.array([-0.5, -0.0, 0.0, 0.5])
+    keys = np.array([0.0, -0.0])
+    lower, upper, gallop = (np.empty(2, dtype=np.int64) for _ in range(3))
+    pair_lib.h_searches(a.ctypes.data, 4, keys.ctypes.data, 2, lower.ctypes.data,
+                        upper.ctypes.data, gallop.ctypes.data)
+    assert lower.tolist() == [2, 1] and upper.tolist() == [3, 2]

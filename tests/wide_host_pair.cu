@@ -198,3 +198,16 @@ extern "C" void h_z_ranges(const double *A, const double *B, long long n, double
         zmax[i] = hi;
     }
 }
+
+// the latitude searches of ranges.cuh over one sorted array: for each key,
+// the first index with a[i] >= key, the first with a[i] > key, and the latter
+// again by galloping forward from the former
+extern "C" void h_searches(const double *a, long long n, const double *keys, long long m,
+                           long long *lower, long long *upper, long long *gallop) {
+    for (long long i = 0; i < m; ++i) {
+        const long long k = sphx::ord64(keys[i]);
+        lower[i] = sphx::lower_bound_ord(a, n, k);
+        upper[i] = sphx::upper_bound_ord(a, n, k);
+        gallop[i] = sphx::upper_bound_ord_from(a, n, lower[i], k);
+    }
+}
