@@ -1,7 +1,7 @@
 // Host builds of the per-pair evaluations (pair_wide, pair_ff2, pair_accux and
 // pair_direct in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
 // arcs.cuh, the adaptive filter in adaptive.cuh and the per-cell band-area
-// routines in areas.cuh are __host__ __device__), exported for tests/test_wide_host.py: the
+// routines in areas.cuh are __host__ __device__), exported for tests/test_host_builds.py: the
 // same source as the GPU kernels, run on the CPU against the exact oracles and
 // the step-by-step FP64 reference. Built with FMA contraction off.
 #include "../paper_2510_09892_gb300/csrc/adaptive.cuh"

@@ -1,5 +1,5 @@
 // Host build of the integer-limb arithmetic (paper_2510_09892_gb300/csrc/wide.cuh
-// compiles for the host as well), exported for tests/test_wide_host.py.
+// compiles for the host as well), exported for tests/test_host_builds.py.
 // A value is passed as three 32-bit limbs (0.M with the top bit set), an
 // exponent and a sign.
 #include "../paper_2510_09892_gb300/csrc/wide.cuh"

@@ -37,10 +37,10 @@ from fractions import Fraction as F
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SRC = os.path.join(ROOT, "tests", "wide_host_harness.cpp")
-OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "wide_host_harness.so")
-PAIR_SRC = os.path.join(ROOT, "tests", "wide_host_pair.cu")
-PAIR_OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "wide_host_pair.so")
+SRC = os.path.join(ROOT, "tests", "host_build_limbs.cpp")
+OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "host_build_limbs.so")
+PAIR_SRC = os.path.join(ROOT, "tests", "host_build_kernels.cu")
+PAIR_OUT = os.path.join(ROOT, "paper_2510_09892_gb300", "_build", "host_build_kernels.so")
 TOP = 1 << 95
 
 
