@@ -1,9 +1,10 @@
-// Host builds of the per-pair evaluations (pair_wide, pair_ff2, pair_accux and
-// pair_direct in paper_2510_09892_gb300/csrc/intersect.cuh, arcs_wide in
-// arcs.cuh, the adaptive filter in adaptive.cuh and the per-cell band-area
-// routines in areas.cuh are __host__ __device__), exported for tests/test_host_builds.py: the
-// same source as the GPU kernels, run on the CPU against the exact oracles and
-// the step-by-step FP64 reference. Built with FMA contraction off.
+// Host builds of the kernels' per-pair and per-cell routines, exported for
+// tests/test_host_builds.py: pair_wide, pair_ff2, pair_accux and pair_direct
+// (paper_2510_09892_gb300/csrc/intersect.cuh), arcs_wide (arcs.cuh), the
+// adaptive filter (adaptive.cuh), the band-area routines (areas.cuh) and the
+// height ranges and latitude searches (ranges.cuh) are __host__ __device__.
+// The same source as the GPU kernels, run on the CPU against the exact
+// oracles and the step-by-step FP64 reference. Built with FMA contraction off.
 #include "../paper_2510_09892_gb300/csrc/adaptive.cuh"
 #include "../paper_2510_09892_gb300/csrc/areas.cuh"
 #include "../paper_2510_09892_gb300/csrc/arcs.cuh"
