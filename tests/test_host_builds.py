@@ -382,7 +382,8 @@ def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
     nbands = inside.sum(axis=1)
     interior = (first > 0) & (first + nbands < nb)
     one = np.flatnonzero((nbands == 1) & interior)
-    two = np.flatnonzero((nbands == 2) & interior & inside[np.arange(F), np.minimum(first + 1, nb - 1)])
+    next_band = inside[np.arange(F), np.minimum(first + 1, nb - 1)]
+    two = np.flatnonzero((nbands == 2) & interior & next_band)
     fan = np.empty(F)
     pair_lib.h_fan_cells(*args, fan.ctypes.data)
     done = one[np.isfinite(fan[one])]
@@ -447,8 +448,8 @@ def test_latitude_searches_on_the_host(pair_lib):
               np.array([0.5]), np.array([], dtype=np.float64)]
     for a in arrays:
         a = np.ascontiguousarray(a[a != 0.0] if len(a) else a, dtype=np.float64)
-        keys = np.concatenate([a, rng.uniform(-1.2, 1.2, 500), np.nextafter(a, 2), np.nextafter(a, -2),
-                               [-1.0, 1.0, 0.0, -0.0, np.inf, -np.inf]]).astype(np.float64)
+        keys = np.concatenate([a, rng.uniform(-1.2, 1.2, 500), np.nextafter(a, 2),
+                               np.nextafter(a, -2), [-1.0, 1.0, 0.0, -0.0, np.inf, -np.inf]])
         m = len(keys)
         lower, upper, gallop = (np.empty(m, dtype=np.int64) for _ in range(3))
         pair_lib.h_searches(a.ctypes.data, len(a), keys.ctypes.data, m, lower.ctypes.data,
