@@ -54,7 +54,6 @@ namespace sphx {
 
 constexpr int kAreaThreads = 128;
 constexpr int64_t kSmemLat = 2048;  // latitudes (and their radii) staged in shared memory up to this count
-constexpr int kFracBits = 80;       // zonal sums: fixed point with 2^-80 resolution
 constexpr int kZonalThreads = 256;
 constexpr int64_t kSmemBands = 3072;  // bands accumulated in shared memory up to this count
 __global__ void band_range_kernel(Mesh m, int32_t *__restrict__ band_lo,
@@ -226,37 +225,7 @@ __global__ void __launch_bounds__(kAreaThreads, 3)
         green_cell<Mode>(m, list[i], band_lo, band_hi, offsets, areas, cap, lat, rho_lat);
 }
 
-// ---- zonal sums in 128-bit fixed point ---------------------------------------------
-// x * 2^80 rounded to an integer (halves away from zero) as a 128-bit two's
-// complement (hi, lo); false for a non-finite x or |x| >= 2^46
-__device__ __forceinline__ bool to_fixed(double x, unsigned long long &lo,
-                                         unsigned long long &hi) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    lo = hi = 0ull;
-    if (ex == 0) return true;  // zero or subnormal: far below 2^-80
-    if (ex == 0x7ff) return false;
-    const unsigned long long M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = ex - 1075 + kFracBits;  // x * 2^80 = M * 2^sh
-    if (sh > 73) return false;             // M * 2^sh >= 2^126
-    if (sh >= 64) {
-        hi = M << (sh - 64);
-    } else if (sh > 0) {
-        lo = M << sh;
-        hi = M >> (64 - sh);
-    } else if (sh == 0) {
-        lo = M;
-    } else if (-sh <= 54) {
-        const int r = -sh;
-        lo = (M + (1ull << (r - 1))) >> r;
-    }
-    if (bits >> 63) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-    }
-    return true;
-}
-
+// ---- zonal sums in 128-bit fixed point (to_fixed, from_fixed: areas.cuh) ------------
 // (hi, lo) += (vhi, vlo) modulo 2^128 with two 64-bit atomics: each wrap of
 // the low word carries once into the high word, whatever the order
 __device__ __forceinline__ void add128(unsigned long long *acc, unsigned long long vlo,
@@ -267,25 +236,6 @@ __device__ __forceinline__ void add128(unsigned long long *acc, unsigned long lo
     if (up) atomicAdd(acc + 1, up);
 }
 
-// the 128-bit fixed-point value as the nearest double
-__device__ __forceinline__ double from_fixed(unsigned long long lo, unsigned long long hi) {
-    const bool neg = (hi >> 63) != 0ull;
-    if (neg) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-    }
-    double v;
-    if (hi == 0ull) {
-        v = ldexp(__ull2double_rn(lo), -kFracBits);
-    } else {
-        const int c = __clzll((long long)hi);
-        unsigned long long top = c ? ((hi << c) | (lo >> (64 - c))) : hi;
-        const unsigned long long rest = lo << c;
-        top |= rest != 0ull ? 1ull : 0ull;  // sticky: below the rounding position
-        v = ldexp(__ull2double_rn(top), 64 - c - kFracBits);
-    }
-    return neg ? -v : v;
-}
 
 __global__ void __launch_bounds__(kZonalThreads)
     zonal_sum_kernel(const int32_t *__restrict__ band_lo, const int32_t *__restrict__ band_hi,

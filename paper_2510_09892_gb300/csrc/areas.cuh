@@ -523,4 +523,73 @@ EFT_HD bool pair_area(const Mesh &m, int64_t f,
     return false;
 }
 
+// ---- zonal sums in 128-bit fixed point ---------------------------------------------
+// a 64-bit integer rounded to the nearest double, and its leading zeros
+EFT_HD double f64_of_u64(unsigned long long x) {
+#if defined(__CUDA_ARCH__)
+    return __ull2double_rn(x);
+#else
+    return (double)x;
+#endif
+}
+
+EFT_HD int clz64(unsigned long long x) {
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+constexpr int kFracBits = 80;  // zonal sums: fixed point with 2^-80 resolution
+
+// x * 2^80 rounded to an integer (halves away from zero) as a 128-bit two's
+// complement (hi, lo); false for a non-finite x or |x| >= 2^46
+EFT_HD bool to_fixed(double x, unsigned long long &lo, unsigned long long &hi) {
+    const unsigned long long bits = (unsigned long long)wide::bits_of(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    lo = hi = 0ull;
+    if (ex == 0) return true;  // zero or subnormal: far below 2^-80
+    if (ex == 0x7ff) return false;
+    const unsigned long long M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = ex - 1075 + kFracBits;  // x * 2^80 = M * 2^sh
+    if (sh > 73) return false;             // M * 2^sh >= 2^126
+    if (sh >= 64) {
+        hi = M << (sh - 64);
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = M >> (64 - sh);
+    } else if (sh == 0) {
+        lo = M;
+    } else if (-sh <= 54) {
+        const int r = -sh;
+        lo = (M + (1ull << (r - 1))) >> r;
+    }
+    if (bits >> 63) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    return true;
+}
+
+// the 128-bit fixed-point value as the nearest double
+EFT_HD double from_fixed(unsigned long long lo, unsigned long long hi) {
+    const bool neg = (hi >> 63) != 0ull;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    double v;
+    if (hi == 0ull) {
+        v = ldexp(f64_of_u64(lo), -kFracBits);
+    } else {
+        const int c = clz64(hi);
+        unsigned long long top = c ? ((hi << c) | (lo >> (64 - c))) : hi;
+        const unsigned long long rest = lo << c;
+        top |= rest != 0ull ? 1ull : 0ull;  // sticky: below the rounding position
+        v = ldexp(f64_of_u64(top), 64 - c - kFracBits);
+    }
+    return neg ? -v : v;
+}
+
 }  // namespace sphx

@@ -212,3 +212,16 @@ extern "C" void h_searches(const double *a, long long n, const double *keys, lon
         gallop[i] = sphx::upper_bound_ord_from(a, n, lower[i], k);
     }
 }
+
+// the zonal sums' fixed point: x * 2^80 rounded (halves away from zero) as a
+// 128-bit two's complement (lo, hi) with ok = 0 where out of range, and a
+// 128-bit value back as the nearest double
+extern "C" void h_to_fixed(const double *x, long long n, unsigned long long *lo,
+                           unsigned long long *hi, int *ok) {
+    for (long long i = 0; i < n; ++i) ok[i] = sphx::to_fixed(x[i], lo[i], hi[i]) ? 1 : 0;
+}
+
+extern "C" void h_from_fixed(const unsigned long long *lo, const unsigned long long *hi,
+                             long long n, double *x) {
+    for (long long i = 0; i < n; ++i) x[i] = sphx::from_fixed(lo[i], hi[i]);
+}

@@ -25,7 +25,10 @@ only, no FMA contraction) and checked on the CPU:
     band-area oracle within 32 u (longitude perimeter + height range);
   * the height range of each arc that decides its candidate latitudes: it
     contains the arc's exact height extent (so no hit is lost) and is widened
-    by no more than the FP32 margin.
+    by no more than the FP32 margin;
+  * the latitude searches, against numpy.searchsorted;
+  * the zonal sums' 128-bit fixed point: each term rounded once to a multiple
+    of 2^-80 (halves away from zero), and a sum back to the nearest double.
 """
 import ctypes
 import os
@@ -188,6 +191,8 @@ def pair_lib():
     L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
     L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp]
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
+    L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
+    L.h_from_fixed.argtypes = [vp, vp, ll, vp]
     return L
 
 
@@ -464,3 +469,41 @@ def test_latitude_searches_on_the_host(pair_lib):
     pair_lib.h_searches(a.ctypes.data, 4, keys.ctypes.data, 2, lower.ctypes.data,
                         upper.ctypes.data, gallop.ctypes.data)
     assert lower.tolist() == [2, 1] and upper.tolist() == [3, 2]
+
+
+def test_zonal_fixed_point_on_the_host(pair_lib):
+    import numpy as np
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(108)
+    x = np.concatenate([
+        rng.standard_normal(2000) * 10.0 ** rng.uniform(-30, 13, 2000),
+        [0.0, -0.0, 5e-324, -5e-324, 2.0 ** -81, 3 * 2.0 ** -82, -3 * 2.0 ** -82, 2.0 ** -80,
+         2.0 ** 45, -(2.0 ** 46) * 0.999, 2.0 ** 46, np.inf, np.nan]])
+    n = len(x)
+    lo, hi = np.empty(n, dtype=np.uint64), np.empty(n, dtype=np.uint64)
+    ok = np.empty(n, dtype=np.int32)
+    pair_lib.h_to_fixed(x.ctypes.data, n, lo.ctypes.data, hi.ctypes.data, ok.ctypes.data)
+    values = []
+    for i in range(n):
+        if not np.isfinite(x[i]) or abs(x[i]) >= 2.0 ** 46:
+            assert ok[i] == 0
+            continue
+        assert ok[i] == 1
+        exact = Fr(float(x[i])) * (1 << 80)
+        q, r = divmod(abs(exact.numerator), exact.denominator)
+        q += 1 if 2 * r >= exact.denominator else 0  # halves away from zero
+        want = -q if exact < 0 else q
+        got = (int(hi[i]) << 64) | int(lo[i])
+        got = got - (1 << 128) if got >> 127 else got
+        assert got == want, (x[i], got, want)
+        values.append(want)
+    # sums of the fixed-point terms (exact integers) back to the nearest double
+    sums = [sum(values[:k]) for k in (1, 7, 100, len(values))] + [-(1 << 120) + 12345, (1 << 100) + 1]
+    sums += [int(v) for v in rng.integers(-(1 << 62), 1 << 62, 500)]
+    m = len(sums)
+    lo2 = np.array([s_ & ((1 << 64) - 1) for s_ in sums], dtype=np.uint64)
+    hi2 = np.array([(s_ >> 64) & ((1 << 64) - 1) for s_ in sums], dtype=np.uint64)
+    out = np.empty(m)
+    pair_lib.h_from_fixed(lo2.ctypes.data, hi2.ctypes.data, m, out.ctypes.data)
+    for s_, got in zip(sums, out):
+        assert got == float(Fr(s_, 1 << 80)), (s_, got)
