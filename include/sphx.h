@@ -17,7 +17,7 @@
  *   s = sqrt(|n_xy|^2 - |n|^2 z0^2),
  * they exist iff |n_xy|^2 >= |n|^2 z0^2 (two when strict, Sec. 2), and a
  * candidate is a hit iff it lies on the arc, decided as (x1 x P).n >= 0 and
- * (P x x2).n >= 0 (the paper only requires "between x1 and x2").
+ * (P x x2).n >= 0 (Sec. 2 only asks for the point to lie between the endpoints).
  * Root slot 0 is the upper sign (the alpha* <= 0 root that Algorithm 8,
  * AccuX, returns); slot 1 the lower sign. A tangent point (s = 0) is one hit
  * in slot 0.

@@ -11,9 +11,9 @@ Contents
 --------
 ``exact``      The plain definition: Eq. 2.2 evaluated in exact rational
                arithmetic (Python integers) on the FP64 inputs taken as exact
-               reals, the "lies between x1 and x2" test decided exactly, and
-               each coordinate correctly rounded to nearest-even FP64
-               (Sec. 1.2, Sec. 2, Sec. 3).
+               reals, the test that a point lies between the endpoints
+               decided exactly, and each coordinate correctly rounded to
+               nearest-even FP64 (Sec. 1.2, Sec. 2, Sec. 3).
 ``steps``      The paper's algorithms executed step by step in FP64 with
                correctly rounded operations (Algorithms 1, 2, 4, 5, 6, 7 and
                8, plus the AccSqrt reading), and the direct FP64 evaluation of

@@ -23,9 +23,10 @@
  *     S == 0 gives (0, 0).
  *  R4 The second root flips the sign of s in Eq. 2.2 (slot 1); the CompDot
  *     of Algorithm 8 then takes -sbar, -e_s in place of sbar, e_s.
- *  R5 Containment ("must lie between x1 and x2", Sec. 2): with the computed
- *     point P and m1 = n x x1, m2 = x2 x n, a candidate is a hit iff
- *     P.m1 >= 0 and P.m2 >= 0 (equal to (x1 x P).n >= 0, (P x x2).n >= 0).
+ *  R5 Containment (Sec. 2 asks only that the point lie between the
+ *     endpoints): with the computed point P and m1 = n x x1, m2 = x2 x n, a
+ *     candidate is a hit iff P.m1 >= 0 and P.m2 >= 0 (equal to
+ *     (x1 x P).n >= 0, (P x x2).n >= 0).
  *     The EFT path forms m1, m2 from the leading parts nbar with FMAs; the
  *     direct path uses its plainly computed n without FMAs.
  *  R6 Existence (Sec. 2): candidates exist iff the computed s^2 >= 0; s^2 == 0

@@ -225,3 +225,15 @@ extern "C" void h_from_fixed(const unsigned long long *lo, const unsigned long l
                              long long n, double *x) {
     for (long long i = 0; i < n; ++i) x[i] = sphx::from_fixed(lo[i], hi[i]);
 }
+
+// Algorithm 8's intermediate pairs (App. A) as the intermediates call dumps
+// them: 16 doubles per arc
+extern "C" void h_accux_mid(const double *A, const double *B, const double *Z, long long n,
+                            double *mid) {
+    for (long long i = 0; i < n; ++i) {
+        const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
+        const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
+        sphx::PairOut o;
+        sphx::pair_accux<true>(x1, x2, Z[i], o, mid + 16 * i);
+    }
+}

@@ -193,6 +193,7 @@ def pair_lib():
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
     L.h_from_fixed.argtypes = [vp, vp, ll, vp]
+    L.h_accux_mid.argtypes = [vp, vp, vp, ll, vp]
     return L
 
 
@@ -507,3 +508,39 @@ def test_zonal_fixed_point_on_the_host(pair_lib):
     pair_lib.h_from_fixed(lo2.ctypes.data, hi2.ctypes.data, m, out.ctypes.data)
     for s_, got in zip(sums, out):
         assert got == float(Fr(s_, 1 << 80)), (s_, got)
+
+
+@pytest.mark.parametrize("axis", [None, 0, 1, 2, "swap"])
+def test_accux_intermediates_and_reflections_on_the_host(pair_lib, axis):
+    """App. A: the kernel's AccuX built for the host carries exactly the step
+    reference's intermediate pairs; and (Sec. 3) reflected or swapped inputs
+    give the reflected outputs bit for bit, the slots exchanged where the
+    s-term of Eq. 2.2 changes sign."""
+    import numpy as np
+    from oracle import steps
+    from paper_2510_09892_gb300 import workloads as W
+    from tests import parity as P
+    from tests.test_oracle_steps import _reflect, equal_as_mapped, expected_after
+    A, B, z = W.uniform_arcs(3000, seed=109)
+    A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
+    n = len(z)
+
+    def run(A_, B_, z_):
+        A_, B_, z_ = (np.ascontiguousarray(v, dtype=np.float64) for v in (A_, B_, z_))
+        pts = np.empty((n, 2, 3))
+        cnt = np.empty(n, dtype=np.int32)
+        pair_lib.h_pair_accux(A_.ctypes.data, B_.ctypes.data, z_.ctypes.data, n,
+                              pts.ctypes.data, cnt.ctypes.data)
+        return cnt, pts
+
+    if axis is None:
+        mid = np.empty((n, 16))
+        pair_lib.h_accux_mid(A.ctypes.data, B.ctypes.data, z.ctypes.data, n, mid.ctypes.data)
+        r = steps.accux_intermediates(A, B, z, variant=2)["raw"]
+        ok = r[:, 10] >= 0
+        assert P.same_bits(mid[ok, :15], r[ok, :15])
+        return
+    c0, p0 = run(A, B, z)
+    c1, p1 = run(B, A, z) if axis == "swap" else run(*_reflect(A, B, z, axis))
+    assert np.array_equal(c0, c1)
+    assert equal_as_mapped(c0, p1, expected_after(p0, axis))

@@ -283,8 +283,8 @@ def equal_as_mapped(c, got, want):
 
 @pytest.mark.parametrize("axis", [0, 1, 2, "swap"])
 def test_step_reference_is_reflection_equivariant(axis):
-    """Sec. 3 reduces the analysis to n >= 0, z0 >= 0 by reflections "without
-    loss of generality". In round-to-nearest arithmetic every step of
+    """Sec. 3 reduces the analysis to n >= 0, z0 >= 0 by reflections, as if
+    nothing were lost by doing so. In round-to-nearest arithmetic every step of
     Algorithm 8 (and of the direct form) commutes with negations and
     operand swaps, so the reduction holds bit for bit."""
     A, B, z = W.stress_arcs(4000, seed=303)
