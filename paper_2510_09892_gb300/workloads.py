@@ -458,3 +458,160 @@ def cells_as_lists(nodes, face_offsets, face_nodes, which=None):
         ids = face_nodes[face_offsets[f]:face_offsets[f + 1]]
         out.append([tuple(float(x) for x in nodes[i]) for i in ids])
     return out
+
+
+# ------------------------------------------------- near-boundary arcs ---------
+# Pythagorean triples (p, q, r): a rotation about the z-axis by atan2(q, p),
+# scaled by r, maps integer vectors to integer vectors exactly (directions, and
+# so latitudes, are all that the intersection depends on).
+_PYTHAGOREAN = ((3, 4, 5), (5, 12, 13), (8, 15, 17), (7, 24, 25), (20, 21, 29),
+                (12, 35, 37), (9, 40, 41), (28, 45, 53), (11, 60, 61), (33, 56, 65))
+
+NEAR_CLASSES = (("tangent", 0.3), ("tangent_rotated", 0.2), ("endpoint_offset", 0.4),
+                ("endpoint_z", 0.1))
+
+
+def _convergents(x, max_den: int):
+    """Continued-fraction convergents p/q of the positive Fraction x with q <= max_den."""
+    from fractions import Fraction
+    out = []
+    p0, q0, p1, q1 = 0, 1, 1, 0
+    num, den = x.numerator, x.denominator
+    while den:
+        a, r = divmod(num, den)
+        p0, p1 = p1, a * p1 + p0
+        q0, q1 = q1, a * q1 + q0
+        if q1 > max_den:
+            break
+        out.append(Fraction(p1, q1))
+        num, den = den, r
+    return out
+
+
+def _near_tangent_one(rng, rotated: bool, log2_range=(80.0, 110.0)):
+    """One arc whose great circle is tangent to the latitude z0 to within
+    |s^2| / |n_xy|^2 = 2^-e, e in log2_range (where constructible).
+
+    The arc lies in the plane through the z-axis direction (a, 0, b) and the
+    y-axis: x1 = (a, Y1, b), x2 = (a, -Y2, b), whose highest point has height
+    b / sqrt(a^2 + b^2). With z0 fixed, a / b is taken from the convergents of
+    sqrt(1 - z0^2) / z0, so that height approaches z0 as closely as integers
+    a, b < 2^52 allow; the relative gap of the squared heights is then an
+    exact rational, and a convergent whose gap lands in the range is kept.
+    The rotated variant keeps a, b, Y < 2^46 and turns the plane about the
+    z-axis by a Pythagorean angle, exactly in integers.
+    """
+    from fractions import Fraction
+    lim = 1 << (45 if rotated else 52)
+    while True:
+        z0 = float(rng.uniform(0.02, 0.98))
+        zf = Fraction(z0)
+        t2 = (1 - zf * zf) / (zf * zf)             # (a / b)^2 at exact tangency
+        k = 320
+        t = Fraction(math.isqrt((t2.numerator << (2 * k)) // t2.denominator), 1 << k)
+        picks = []
+        for c in _convergents(t, lim):
+            a, b = c.numerator, c.denominator
+            if a >= lim or a == 0:
+                continue
+            gap = (1 - zf * zf) - zf * zf * Fraction(a * a, b * b)   # s^2 / |n_xy|^2
+            if gap == 0:
+                continue
+            e = -math.log2(abs(gap.numerator) / gap.denominator)
+            if log2_range[0] <= e <= log2_range[1]:
+                picks.append((a, b))
+        if picks:
+            a, b = picks[int(rng.integers(len(picks)))]
+            break
+    if rotated:
+        y1 = int(b * rng.uniform(0.05, 1.5)) + 1
+        y2 = int(b * rng.uniform(0.05, 1.5)) + 1
+        p, q, r = _PYTHAGOREAN[int(rng.integers(len(_PYTHAGOREAN)))]
+        v1 = [p * a - q * y1, q * a + p * y1, r * b]
+        v2 = [p * a + q * y2, q * a - p * y2, r * b]
+    else:
+        y1 = float(b) * rng.uniform(0.05, 1.5)
+        y2 = float(b) * rng.uniform(0.05, 1.5)
+        v1 = [a, y1, b]
+        v2 = [a, -y2, b]
+    x1 = np.array(v1, dtype=np.float64)
+    x2 = np.array(v2, dtype=np.float64)
+    # exact symmetries of the square about the z-axis
+    if rng.random() < 0.5:
+        x1[[0, 1]] = x1[[1, 0]]
+        x2[[0, 1]] = x2[[1, 0]]
+    for ax in (0, 1):
+        if rng.random() < 0.5:
+            x1[ax], x2[ax] = -x1[ax], -x2[ax]
+    if rng.random() < 0.5:                          # mirror to the south
+        x1[2], x2[2], z0 = -x1[2], -x2[2], -z0
+    # powers of two bring the endpoints near unit length (exact)
+    x1 = np.ldexp(x1, -int(np.frexp(np.abs(x1).max())[1]))
+    x2 = np.ldexp(x2, -int(np.frexp(np.abs(x2).max())[1]))
+    if rng.random() < 0.5:
+        x1, x2 = x2, x1
+    return x1, x2, z0
+
+
+def near_boundary_arcs(n: int, seed: int = DEFAULT_SEED + 7, return_class: bool = False):
+    """Arcs at the two decision boundaries of the method (Sec. 2: whether the
+    circles meet, and whether a candidate lies between the endpoints):
+
+    * ``tangent`` (30 %): great circles tangent to their latitude to within
+      |s^2| / |n_xy|^2 of 2^-80 .. 2^-104 (integer-ratio construction, see
+      _near_tangent_one), both signs, with the apex inside the arc;
+    * ``tangent_rotated`` (20 %): the same, turned about the z-axis by a
+      Pythagorean angle (gaps 2^-80 .. about 2^-92);
+    * ``endpoint_offset`` (40 %): arcs of length U(0.01, pi/2) whose latitude
+      passes 2^-45 .. 2^-30 rad (log-uniform) inside or outside one endpoint
+      along the arc (placed where the height changes by >= 0.1 per radian);
+    * ``endpoint_z`` (10 %): z0 equal to one endpoint's z, bit for bit
+      (the candidate sits within rounding of the endpoint), a fifth of them
+      with an exactly unit endpoint on the equator and z0 = 0 (the candidate
+      is that endpoint).
+    """
+    rng = np.random.default_rng(seed)
+    counts = [int(round(n * w)) for _, w in NEAR_CLASSES]
+    counts[0] += n - sum(counts)
+    klass = np.concatenate([np.full(c, i, dtype=np.int8) for i, c in enumerate(counts)])
+    klass = klass[rng.permutation(n)]
+    A = np.empty((n, 3))
+    B = np.empty((n, 3))
+    z = np.empty(n)
+    for i in range(n):
+        k = NEAR_CLASSES[klass[i]][0]
+        if k in ("tangent", "tangent_rotated"):
+            A[i], B[i], z[i] = _near_tangent_one(rng, k == "tangent_rotated")
+            continue
+        while True:
+            a = _random_unit(rng, 1)
+            b = _orthonormal_partner(rng, a)
+            a, b = a[0], b[0]
+            L = float(rng.uniform(0.01, np.pi / 2))
+            end = int(rng.integers(2))
+            te = 0.0 if end == 0 else L
+            slope = -math.sin(te) * a[2] + math.cos(te) * b[2]
+            if abs(slope) >= 0.1:
+                break
+        x1 = a
+        x2 = math.cos(L) * a + math.sin(L) * b
+        if k == "endpoint_offset":
+            d = 2.0 ** rng.uniform(-45, -30) * (1 if rng.random() < 0.5 else -1)
+            t = d if end == 0 else L - d                 # d > 0: inside the arc
+            if end == 0:
+                zz = a[2] + d * b[2] - 0.5 * d * d * a[2]
+            else:
+                zz = math.cos(t) * a[2] + math.sin(t) * b[2]
+        else:
+            if rng.random() < 0.2:
+                ax = int(rng.integers(2))
+                x1 = np.zeros(3)
+                x1[ax] = 1.0 if rng.random() < 0.5 else -1.0
+                zz = 0.0
+            else:
+                zz = (x1 if end == 0 else x2)[2]
+        A[i], B[i], z[i] = x1, x2, zz
+    out = (np.ascontiguousarray(A), np.ascontiguousarray(B), np.ascontiguousarray(z))
+    if return_class:
+        return out + (klass,)
+    return out

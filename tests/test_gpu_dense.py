@@ -38,6 +38,7 @@ def run(A, B, z, mode):
 
 def check_against_exact(cnt, pts, A, B, z, ulp_gate=4.0):
     ce, pe, fe = P.run_exact(A, B, z)
+    P.assert_unflagged(fe)
     ok = fe == 0
     assert np.array_equal(cnt[ok], ce[ok]), np.flatnonzero((cnt != ce) & ok)[:10]
     hit = np.isfinite(pe[..., 0]) & ok[:, None]
@@ -205,6 +206,7 @@ def test_ff32_within_stated_bound(gen):
         A, B, z = W.stress_arcs(10_000, seed=32)
     cnt, pts = run(A, B, z, "ff32")
     ce, pe, fe = P.run_exact(A, B, z)
+    P.assert_unflagged(fe)
     ok = fe == 0
     bound = P.ff_bound(A, B, z)
     hit = np.isfinite(pe[..., 0]) & np.isfinite(pts[..., 0]) & ok[:, None]
@@ -425,6 +427,7 @@ def test_error_distribution_report():
     for name, (A, B, z) in (("uniform", W.uniform_arcs(20_000, seed=14)),
                             ("stress", W.stress_arcs(20_000, seed=13))):
         ce, pe, fe = P.run_exact(A, B, z)
+        P.assert_unflagged(fe)
         ok = fe == 0
         for mode in ("wide", "eft", "direct", "ff32"):
             cnt, pts = run(A, B, z, mode)

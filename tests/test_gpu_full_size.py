@@ -99,6 +99,7 @@ def test_full_size_mixed_workload(full_batch):
     _properties(pw, cw, tz)
     # the exact oracle on the sample (integer limbs: <= 1 ulp, exact counts)
     ce, pe, fe = P.run_exact(sA, sB, sz)
+    P.assert_unflagged(fe)
     ok = fe == 0
     idx = torch.from_numpy(sample).to(DEV)
     c_s = cw[idx].cpu().numpy()
@@ -251,6 +252,7 @@ def test_full_size_ragged_meshes(full_ragged):
         assert a[:3] == b[:3] and P.same_bits(a[3:], b[3:])
     # the exact oracle on every (sampled edge, latitude) pair
     ce, pex, fe = P.run_exact(A, B, z)
+    P.assert_unflagged(fe)
     pair_of = {(int(sample[pe[j]]), int(pk[j])): j for j in range(len(pe))}
     wp = np.full((len(pe), 2, 3), np.nan)
     for x in got_w:

@@ -121,6 +121,10 @@ def test_small_meshes_against_exact_oracle(ctx, mode):
     wk = {(e, k, r): (x, yy) for e, k, r, x, yy in want}
     gk, gx, gy = sorted_records(recs)
     got = {tuple(int(v) for v in gk[i]): (gx[i], gy[i]) for i in range(len(gk))}
+    pairs = sum(int(eo1 - eo0) * int(lo1 - lo0) for eo0, eo1, lo0, lo1 in zip(
+        batch["edge_offsets"][:-1], batch["edge_offsets"][1:],
+        batch["lat_offsets"][:-1], batch["lat_offsets"][1:]))
+    assert len(flagged) <= (1 - P.MIN_UNFLAGGED) * pairs
     # identical hit sets except on pairs the oracle flags as near a boundary
     diff = set(wk) ^ set(got)
     assert all((e, k) in flagged for e, k, _ in diff), sorted(diff)[:5]
