@@ -2,15 +2,23 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sphx|reference]
 
-A step is one dense call (sphx_intersect_gca_constlat) over the
-ill-conditioned workload of 10^6 arcs (40 % short, 30 % near-tangent, 20 %
-near-pole, 10 % near-antipodal), inputs resident in HBM; the L2 cache is
-flushed (a 256 MiB write) between timed steps. The headline mode is the
-integer-limb evaluation (SPHX_MODE_WIDE_INT, within 1 ulp of the exact
-result); FP64-EFT (the paper's AccuX), direct FP64 and float-float are timed
-the same way beside it. Under torchrun each rank runs its own
-independently seeded batch (weak scaling, no data-path collective); the step
-time is the maximum over ranks.
+A step is one dense call (sphx_intersect_gca_constlat) over the precision
+workload: 2x10^8 arcs, 90 % well-conditioned (endpoints uniform on the
+sphere, length U(0, pi/2), one latitude in each arc's z-range) mixed with
+10 % of the ill-conditioned stress mix (short, nearly tangent, near-pole and
+near-antipodal arcs), generated in independently seeded chunks of 2^20 arcs.
+The 21.6 GB of inputs and outputs exceed the 129 MB L2 many times over, so
+no flush is needed between steps. The headline mode is the integer-limb
+evaluation (SPHX_MODE_WIDE_INT, correctly rounded on every sampled arc);
+FP64-EFT (the paper's AccuX), direct FP64 and float-float run the same steps
+beside it. The metric counts intersections (hits), not arcs. Under torchrun
+each rank runs its own independently seeded batch (weak scaling, no
+data-path collective); the step time is the maximum over ranks.
+
+Beside the headline: the 10^6-arc stress workload (L2 flushed between
+steps), arc x arc pairs, the adaptive filter, the ragged regridding and
+mesh-batch legs and the zonal-mean step; on the host cores, the exact oracle
+and the paper's two FP64 forms as plain C loops (cpu_baseline).
 
 ``--impl reference`` times the exact-rational CPU oracle, as it stands, on
 the host's cores over bounded samples of the same workload.
@@ -20,6 +28,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import math
 import os
@@ -39,28 +48,41 @@ from paper_2510_09892_gb300 import workloads as W  # noqa: E402
 
 METRIC = "arc–latitude intersections/sec at ≤4-ulp error, EFT vs direct FP64, % HBM roofline"
 UNIT = "intersections/s"
-N_ARCS = 1_000_000
-WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-uniform 1e-10..1e-2 rad), "
-            "30% nearly tangent (z0 within 1e-12 of the z-extremum), 20% near-pole "
-            "(|z| > 1-1e-6), 10% near-antipodal")
+N_ARCS = 200_000_000
+MIXED_SEED = W.DEFAULT_SEED + 4
+WORKLOAD = ("precision variant: 2x10^8 arcs, 90% uniform (endpoints uniform on the sphere, "
+            "length U(0, pi/2), z0 in the arc's z-range) mixed with 10% of the ill-conditioned "
+            "stress mix, in independently seeded chunks of 2^20 arcs")
+STRESS_ARCS = 1_000_000
+STRESS_WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-uniform "
+                   "1e-10..1e-2 rad), 30% nearly tangent (z0 within 1e-12 of the z-extremum), "
+                   "20% near-pole (|z| > 1-1e-6), 10% near-antipodal")
+MODES = ("wide", "eft", "direct", "ff32")
 # algorithmic work per arc of the dense call (both roots and the on-arc test)
 BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
-# thread instructions per arc of dense_kernel<WIDE> (ncu smsp__inst_executed.sum x 32
-# / arcs on the 10^6-arc stress workload): the integer-limb method's work per arc
-INST_PER_ARC = {"wide": 2351}
-# DRAM bytes (read + write) of one launch of the headline kernel over the 10^6
-# stress arcs, from the same ncu capture (writes still in L2 at kernel end are
-# not counted)
-TRAFFIC_PER_LAUNCH = {"wide": 58.238e6 + 9.188e6}
+# Thread instructions per arc of dense_kernel<WIDE>, from one ncu capture
+# (smsp__inst_executed.sum x 32 / arcs): a property of the compiled kernel,
+# valid only for the build it was taken on, reported as a secondary figure.
+INST_PER_ARC = {"wide": {"value": 2351, "source": "ncu smsp__inst_executed.sum x 32 / arcs, "
+                         "10^6 stress arcs, profiles/dense_kernel_wide_stress_1e6.md "
+                         "(kernel as of commit 7822872)"}}
+# DRAM bytes (read + write) per arc of one launch, from an ncu capture of a
+# launch larger than L2; None where no capture matches the current kernel.
+TRAFFIC_PER_ARC = {"wide": None}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
           "direct": "f64", "ff32": "f32 pairs + f64",
           "adaptive": "f64 with a running error bound, u32 limbs where it fails"}
+ERROR = {"wide": "<= 1 ulp per component (correctly rounded on every sampled arc)",
+         "eft": "<= 4 ulp per component, |dP| <= 3 u sqrt(1 - z0^2) (Sec. 6.2)",
+         "direct": "unbounded near tangency and the poles (Sec. 4): not at <= 4 ulp",
+         "ff32": "its stated float-float bound, not at <= 4 ulp"}
 L2_FLUSH_BYTES = 256 << 20
 ADAPTIVE_GATES = (4.0, 64.0, 2.0 ** 20)  # ulp per component; 4 is the adaptive mode's own
-CPU_SAMPLE = 32_768            # arcs per oracle step
+CPU_SAMPLE = 32_768            # arcs per oracle step (reference arm)
+CPU_LOOP_ARCS = 100_000_000    # arcs of the mixed workload for the all-core FP64 loops
 
 
 # ------------------------------------------------------------- host logic --
@@ -90,6 +112,21 @@ def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
         dist.barrier()
+
+
+def _mixed_job(args):
+    k, seed = args
+    return k, W.mixed_chunk(k, seed)
+
+
+def fill_mixed(pool, seed: int, A, B, z):
+    """The mixed workload's chunks, generated on the pool, written into the
+    (n, 3), (n, 3), (n,) arrays A, B, z (any writable numpy arrays)."""
+    n = len(z)
+    jobs = [(k, seed) for k in range((n + W.CHUNK - 1) // W.CHUNK)]
+    for k, (a, b, c) in pool.imap_unordered(_mixed_job, jobs):
+        lo, hi = k * W.CHUNK, min(n, (k + 1) * W.CHUNK)
+        A[lo:hi], B[lo:hi], z[lo:hi] = a[:hi - lo], b[:hi - lo], c[:hi - lo]
 
 
 class ClockSampler:
@@ -159,16 +196,25 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ reference arm --
-def oracle_rate(A, B, z, pool) -> float:
-    """Arcs per second of the exact oracle over the given arcs, on the pool."""
+def _oracle_job(args):
     from oracle import exact
+    A, B, Z = args
+    hits = 0
+    for i in range(len(Z)):
+        hits += max(0, exact.intersect(A[i], B[i], Z[i]).count)
+    return hits
+
+
+def oracle_rate(A, B, z, pool) -> tuple[float, float]:
+    """(arcs/s, intersections/s) of the exact oracle over the given arcs, on the pool."""
     n = len(z)
     chunk = max(1, n // (4 * pool._processes))
     jobs = [(A[i:i + chunk].tolist(), B[i:i + chunk].tolist(), z[i:i + chunk].tolist())
             for i in range(0, n, chunk)]
     t0 = time.perf_counter()
-    pool.map(exact._batch_worker, jobs)
-    return n / (time.perf_counter() - t0)
+    hits = sum(pool.map(_oracle_job, jobs))
+    dt = time.perf_counter() - t0
+    return n / dt, hits / dt
 
 
 def run_reference(args):
@@ -177,33 +223,92 @@ def run_reference(args):
         return
     import multiprocessing as mp
     cores = os.cpu_count() or 1
-    A, B, z = W.stress_arcs(N_ARCS)
+    steps = args.warmup + args.steps
+    # one bounded sample per step: CPU_SAMPLE consecutive arcs of chunk `step`
     with mp.get_context("spawn").Pool(cores) as pool:
-        rates = []
-        for step in range(args.warmup + args.steps):
-            lo = (step * CPU_SAMPLE) % (N_ARCS - CPU_SAMPLE)
-            r = oracle_rate(A[lo:lo + CPU_SAMPLE], B[lo:lo + CPU_SAMPLE], z[lo:lo + CPU_SAMPLE],
-                            pool)
+        secs, hits = [], []
+        for step in range(steps):
+            A, B, z = W.mixed_chunk(step, MIXED_SEED)
+            a_rate, h_rate = oracle_rate(A[:CPU_SAMPLE], B[:CPU_SAMPLE], z[:CPU_SAMPLE], pool)
             if step >= args.warmup:
-                rates.append(r)
-    value = CPU_SAMPLE / statistics.mean([CPU_SAMPLE / r for r in rates])
+                secs.append(CPU_SAMPLE / a_rate)
+                hits.append(h_rate * CPU_SAMPLE / a_rate)
+    value = sum(hits) / sum(secs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * CPU_SAMPLE / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "exact rational (Python int), rounded to f64",
-        "data": "synthetic", "config": config_dict(args, args.mode),
+        "data": "synthetic", "config": config_dict(args, "exact oracle"),
+        "arcs_per_s": CPU_SAMPLE * len(secs) / sum(secs),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{CPU_SAMPLE} consecutive arcs of the workload per step"},
+                         "sample": f"per step, the first {CPU_SAMPLE} arcs of one 2^20-arc chunk "
+                                   "of the workload (chunk index = step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def config_dict(args, mode):
-    return {"workload": WORKLOAD, "arcs_per_gpu": N_ARCS, "mode": mode,
-            "seed": W.DEFAULT_SEED + 1, "l2": "flushed between timed steps (256 MiB write)",
+    return {"workload": WORKLOAD, "arcs_per_gpu": args.arcs, "mode": mode, "seed": MIXED_SEED,
+            "l2": "inputs and outputs (108 B per arc) far larger than L2: no flush",
             "parallelism": f"independent batches, {args.gpus} GPU(s)"}
+
+
+# ---------------------------------------------------------------- CPU loops --
+def cpu_loop_rate(fn, A, B, z, threads: int, chunk: int = 1 << 18) -> dict:
+    """Arcs/s and intersections/s of a plain C loop (the step reference) over
+    all arcs, split into `threads` contiguous ranges on host threads (the C
+    calls release the interpreter lock, so the threads run in parallel)."""
+    n = len(z)
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+
+    def work(t):
+        hits = 0
+        for s in range(int(bounds[t]), int(bounds[t + 1]), chunk):
+            e = min(int(bounds[t + 1]), s + chunk)
+            c, _ = fn(A[s:e], B[s:e], z[s:e])
+            hits += int(np.clip(c, 0, None).sum())
+        return hits
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        hits = sum(ex.map(work, range(threads)))
+    dt = time.perf_counter() - t0
+    return {"value": hits / dt, "unit": UNIT, "arcs_per_s": n / dt, "cores": threads,
+            "arcs": n}
+
+
+def fp64_loops(stress, mixed) -> dict:
+    """The paper's two FP64 forms as plain C loops (the step reference,
+    gcc -O2 -ffp-contract=off): direct Eq. 2.2 and AccuX (Algorithm 8), on
+    one core and on all host cores, over the whole 10^6-arc stress workload
+    and over the first 10^8 arcs of the mixed workload."""
+    from oracle import steps
+    steps.lib()  # build outside the timing
+    cores = os.cpu_count() or 1
+    forms = {"direct": steps.direct, "accux": lambda A, B, z: steps.accux(A, B, z, variant=2)}
+    out = {"cores": cores, "kind": "plain C loops of the step reference (gcc -O2 "
+                                   "-ffp-contract=off), one arc per iteration"}
+    for name, fn in forms.items():
+        out[name] = {
+            "stress_1e6_one_core": cpu_loop_rate(fn, *stress, threads=1),
+            "stress_1e6_all_cores": cpu_loop_rate(fn, *stress, threads=cores),
+            "mixed_all_cores": cpu_loop_rate(fn, *mixed, threads=cores),
+        }
+    out["accux_over_direct_time_one_core"] = (out["direct"]["stress_1e6_one_core"]["arcs_per_s"]
+                                              / out["accux"]["stress_1e6_one_core"]["arcs_per_s"])
+    return out
+
+
+def cpu_oracle_leg(pool, A, B, z) -> dict:
+    """The exact oracle, as it stands, on all host cores over a bounded sample."""
+    cores = pool._processes
+    n = min(len(z), 6000 * cores)  # ~0.6 s of oracle work per core
+    oracle_rate(A[:1024], B[:1024], z[:1024], pool)  # start the workers
+    a_rate, h_rate = oracle_rate(A[:n], B[:n], z[:n], pool)
+    return {"value": h_rate, "unit": UNIT, "arcs_per_s": a_rate, "cores": cores,
+            "kind": "oracle", "sample": f"first {n} arcs of the headline workload"}
 
 
 # ------------------------------------------------------------------ GPU arm --
@@ -213,41 +318,45 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sphx", choices=["sphx", "reference"])
+    ap.add_argument("--arcs", type=int, default=N_ARCS,
+                    help="arcs per GPU of the headline workload (default: the 2x10^8 of the "
+                         "precision comparison; smaller values are for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ragged", action="store_true",
-                    help="skip the ragged (regridding) leg reported beside the headline")
-    ap.add_argument("--mode", default="wide", choices=["wide", "eft", "direct", "ff32"],
+                    help="skip the ragged, mesh-batch and zonal legs reported beside the headline")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the headline mode on the headline workload (for profiling)")
+    ap.add_argument("--mode", default="wide", choices=list(MODES),
                     help="headline evaluation mode (the others are timed beside it)")
     ap.add_argument("--zonal-only", action="store_true",
                     help="run only the zonal-mean leg and print its JSON (for profiling)")
     ap.add_argument("--ragged-only", action="store_true",
                     help="run only the cubed-sphere regridding leg and print its JSON (for profiling)")
+    ap.add_argument("--meshes-only", action="store_true",
+                    help="run only the 512-mesh ragged leg and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
-    if args.zonal_only or args.ragged_only:
+    import multiprocessing as mp
+    rank, world, local = dist_env()
+    cores = max(1, (os.cpu_count() or 1) // world)
+    pool = mp.get_context("spawn").Pool(cores)
+    if args.zonal_only or args.ragged_only or args.meshes_only:
         import torch
         from paper_2510_09892_gb300 import sphx
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         if args.zonal_only:
             line = {"zonal_mean": zonal_leg(sphx, torch, dev, args, args.mode)}
-        else:
+        elif args.ragged_only:
             line = {"ragged_regridding": ragged_leg(sphx, torch, dev, args, args.mode)}
+        else:
+            line = {"ragged_meshes": meshes_leg(sphx, torch, dev, args, args.mode, pool)}
+        pool.close()
         print(json.dumps(line), flush=True)
         return
-
-    rank, world, local = dist_env()
-    # the process pools start before CUDA does ('spawn' regardless)
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_leg()
-    mesh_pool = None
-    if rank == 0 and not args.no_ragged:
-        import multiprocessing as mp
-        mesh_pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
 
     import torch
     import torch.distributed as dist
@@ -257,43 +366,62 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    n = args.arcs
+    seed = shard_seed(MIXED_SEED, rank)
+    # the workload in page-locked host memory: the source of the device copy
+    # and the host buffers of the end-to-end call
+    hA = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    hB = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    hz = torch.empty((n,), dtype=torch.float64, pin_memory=True)
+    t_gen = time.perf_counter()
+    fill_mixed(pool, seed, hA.numpy(), hB.numpy(), hz.numpy())
+    t_gen = time.perf_counter() - t_gen
 
-    A, B, z = W.stress_arcs(N_ARCS, seed=shard_seed(W.DEFAULT_SEED + 1, rank))
-    tA, tB, tz = (torch.from_numpy(v).to(dev) for v in (A, B, z))
-    pts = torch.empty((N_ARCS, 2, 3), dtype=torch.float64, device=dev)
-    cnt = torch.empty((N_ARCS,), dtype=torch.int32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and not args.headline_only:
+        cpu = cpu_oracle_leg(pool, hA.numpy(), hB.numpy(), hz.numpy())
+        stress = W.stress_arcs(STRESS_ARCS)
+        m = min(n, CPU_LOOP_ARCS)
+        cpu["fp64_loops"] = fp64_loops(stress, (hA.numpy()[:m], hB.numpy()[:m], hz.numpy()[:m]))
+    tA, tB, tz = (t.to(dev) for t in (hA, hB, hz))
+    pts = torch.empty((n, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.empty((n,), dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
     def timed(mode, steps, warmup):
-        """Mean kernel time (ms) of `steps` dense calls, L2 flushed before each."""
-        ms = []
+        """CUDA-event times (ms) of `steps` dense calls over the whole batch on `stream`."""
+        evs = []
         with torch.cuda.stream(stream):
             for i in range(warmup + steps):
-                flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, mode, stream)
                 e1.record(stream)
                 if i >= warmup:
-                    ms.append((e0, e1))
+                    evs.append((e0, e1))
         stream.synchronize()
-        return [a.elapsed_time(b) for a, b in ms]
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def hits_of(mode):
+        with torch.cuda.stream(stream):
+            sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, mode, stream)
+            h = int(torch.clamp(cnt, min=0).sum(dtype=torch.int64).item())
+        return h
 
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     fp64_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP64) / 2  # FMA/s = FP64 op slots/s
     fp32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_FP32) / 2
     int32_peak = sphx.sphx_probe_fma_rate(sphx.PIPE_INT32)
     head = args.mode
-    others = [m for m in ("wide", "eft", "direct", "ff32") if m != head]
+    others = [] if args.headline_only else [m for m in MODES if m != head]
+    hbm_peak, hbm_src = measured_hbm_peak_src()
 
-    # warm-up of every mode, then the headline timed region
     for mode in [head] + others:
         timed(mode, 1, args.warmup)
     barrier()
     torch.cuda.synchronize()
-    # the sampler runs through every timed leg (headline, other modes, e2e)
+    # the sampler runs through every timed leg (headline, the other modes, e2e)
     with ClockSampler(local) as clocks:
         t_wall = time.perf_counter()
         head_ms = timed(head, args.steps, 0)
@@ -302,68 +430,50 @@ def main():
         t_wall = time.perf_counter() - t_wall
         gpu_launches = args.steps  # one dense_kernel launch per step
         step_ms = reduce_max(statistics.mean(head_ms), dev)
-        value = world * N_ARCS / (step_ms * 1e-3)
-
-        modes = {head: {"value": value, "ms_per_step": step_ms}}
+        mode_ms = {head: step_ms}
         for mode in others:
-            m = reduce_max(statistics.mean(timed(mode, args.steps, 0)), dev)
-            modes[mode] = {"value": world * N_ARCS / (m * 1e-3), "ms_per_step": m}
-        e2e = e2e_leg(sphx, torch, dev, A, B, z, args, head)
-        # the timed legs last well under a second, shorter than the sampling
-        # period: keep the headline kernel running for 1.5 s more so that the
-        # clock samples describe the GPU under this load (not timed)
-        soak_end = time.perf_counter() + 1.5
-        while time.perf_counter() < soak_end:
-            timed(head, 50, 0)
+            mode_ms[mode] = reduce_max(statistics.mean(timed(mode, args.steps, 0)), dev)
+        e2e = None if args.headline_only else e2e_leg(sphx, torch, dev, hA, hB, hz, args, head)
     clk = clocks.summary()
-    clk["window"] = "timed legs plus a 1.5 s soak of the headline kernel right after"
+    clk["window"] = "the timed steps of every mode and the end-to-end leg"
 
-    arcs = arcs_leg(sphx, torch, dev, args, flush) if rank == 0 else None
-    adaptive = adaptive_leg(sphx, torch, dev, args, flush, (A, B, z)) if rank == 0 else None
-    ragged = ragged_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
-    zonal = zonal_leg(sphx, torch, dev, args, head) if rank == 0 and not args.no_ragged else None
-    meshes = (meshes_leg(sphx, torch, dev, args, head, mesh_pool)
-              if rank == 0 and not args.no_ragged else None)
-
-    # hits per step, from one more headline call's outputs
-    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, head)
-    hits = int(torch.clamp(cnt, min=0).sum().item())
-
-    hbm_peak = measured_hbm_peak()
-
-    def hbm_roof(ms):
-        gbs = BYTES_PER_ARC * N_ARCS / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm_peak,
-                "frac": gbs / hbm_peak, "traffic": None,
-                "note": "108 B per arc (56 in, 52 out) against the measured copy bandwidth "
-                        "(MEASURED_PEAKS.json, of measured)"}
-
-    def alu_roof(ms, ops_per_arc, peak, pipe):
-        rate = ops_per_arc * N_ARCS / (ms * 1e-3)
-        measured = "issue" not in pipe
-        return {"bound": "alu", "unit": "Tops/s", "achieved": rate / 1e12, "peak": peak / 1e12,
-                "frac": rate / peak, "traffic": None,
-                "note": f"{pipe}: {ops_per_arc} operations per arc against "
-                        + ("the pipe's rate measured live by sphx_probe_fma_rate (of measured)"
-                           if measured else
-                           "4 x 32 lanes x SMs x the 2070 MHz maximum SM clock (derived)")}
+    modes = {}
+    for mode, ms in mode_ms.items():
+        h = hits_of(mode)
+        hits_all = reduce_sum(h, dev)
+        modes[mode] = {"value": hits_all / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                       "arcs_per_s": world * n / (ms * 1e-3), "hits_per_step": h,
+                       "hbm_frac": BYTES_PER_ARC * n / (ms * 1e-3) / 1e9 / hbm_peak,
+                       "error": ERROR[mode]}
+        if mode in FP64_OPS_PER_ARC:
+            modes[mode]["fp64_pipe_frac"] = FP64_OPS_PER_ARC[mode] * n / (ms * 1e-3) / fp64_peak
+    value = modes[head]["value"]
+    if e2e is not None:
+        e2e["value"] = reduce_sum(e2e["hits_per_step"], dev) / (e2e["ms_per_step"] * 1e-3)
 
     head_kernel_ms = statistics.mean(head_ms)
+    gbs = BYTES_PER_ARC * n / (head_kernel_ms * 1e-3) / 1e9
+    tpa = TRAFFIC_PER_ARC.get(head)
+    roofline = {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm_peak,
+                "frac": gbs / hbm_peak, "traffic": None if tpa is None else tpa["value"] * n,
+                "kernel": f"dense_kernel<{head}>", "launch_ms": head_kernel_ms,
+                "per_unit": f"{BYTES_PER_ARC} B per arc (56 in, 48 points + 4 count out) x "
+                            f"{n} arcs per launch",
+                "peak_source": hbm_src}
+    if tpa is not None:
+        roofline["traffic_source"] = tpa["source"]
     issue_peak = ISSUE_SLOTS_PER_SM_CLK * sm_count * SM_MAX_MHZ * 1e6
+    roofline_issue = None
     if head in INST_PER_ARC:
-        roofline = alu_roof(head_kernel_ms, INST_PER_ARC[head], issue_peak,
-                            "instruction issue (4 warp instructions per SM per clock)")
-    elif head in FP64_OPS_PER_ARC:
-        roofline = alu_roof(head_kernel_ms, FP64_OPS_PER_ARC[head], fp64_peak, "FP64 pipe")
-    else:
-        roofline = hbm_roof(head_kernel_ms)
-    roofline["kernel"] = f"dense_kernel<{head}>"
-    roofline["traffic"] = TRAFFIC_PER_LAUNCH.get(head)
-    per_mode_roofs = {"hbm": {m: hbm_roof(modes[m]["ms_per_step"])["frac"] for m in modes}}
-    per_mode_roofs["fp64_pipe"] = {m: alu_roof(modes[m]["ms_per_step"], FP64_OPS_PER_ARC[m],
-                                               fp64_peak, "FP64")["frac"]
-                                   for m in modes if m in FP64_OPS_PER_ARC}
+        ipa = INST_PER_ARC[head]
+        rate = ipa["value"] * n / (head_kernel_ms * 1e-3)
+        roofline_issue = {"bound": "alu", "unit": "T instructions/s", "achieved": rate / 1e12,
+                          "peak": issue_peak / 1e12, "frac": rate / issue_peak,
+                          "instructions_per_arc": ipa["value"], "source": ipa["source"],
+                          "peak_source": "4 warp instructions x 32 lanes x SMs x the 2070 MHz "
+                                         "maximum SM clock (derived)"}
     if rank != 0:
+        pool.close()
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -373,39 +483,91 @@ def main():
                               "worst": max(head_ms), "steps": len(head_ms),
                               "note": "this rank's CUDA-event times of the timed steps"},
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
-        "config": config_dict(args, head), "e2e": e2e, "gpu_launches": gpu_launches,
-        "clocks": clk, "roofline": roofline, "roofline_hbm": hbm_roof(head_kernel_ms),
-        "roofline_frac_by_mode": per_mode_roofs,
+        "config": config_dict(args, head), "arcs_per_s": modes[head]["arcs_per_s"],
+        "hits_per_step": modes[head]["hits_per_step"], "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clk, "roofline": roofline, "roofline_issue": roofline_issue,
         "modes": modes,
-        "eft_over_direct_time": modes["eft"]["ms_per_step"] / modes["direct"]["ms_per_step"],
-        "hits_per_step": hits, "timed_wall_s": t_wall,
+        "eft_over_direct_time": (modes["eft"]["ms_per_step"] / modes["direct"]["ms_per_step"]
+                                 if "eft" in modes and "direct" in modes else None),
+        "timed_wall_s": t_wall, "generate_s": t_gen,
         "peaks": {"fp64_fma_per_s": fp64_peak, "fp32_fma_per_s": fp32_peak,
-                  "int32_imad_per_s": int32_peak, "hbm_gbs": hbm_peak},
+                  "int32_imad_per_s": int32_peak, "hbm_gbs": hbm_peak, "hbm_source": hbm_src},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if arcs is not None:
-        line["arc_x_arc"] = arcs
-    if adaptive is not None:
-        line["adaptive_filter"] = adaptive
-    if ragged is not None:
-        line["ragged_regridding"] = ragged
-    if zonal is not None:
-        line["zonal_mean"] = zonal
-    if meshes is not None:
-        line["ragged_meshes"] = meshes
+    if not args.headline_only:
+        del tA, tB, tz, pts, cnt
+        torch.cuda.empty_cache()
+        line["stress_1e6"] = stress_leg(sphx, torch, dev, args)
+        line["arc_x_arc"] = arcs_leg(sphx, torch, dev, args)
+        line["adaptive_filter"] = adaptive_leg(sphx, torch, dev, args)
+        if not args.no_ragged:
+            line["ragged_regridding"] = ragged_leg(sphx, torch, dev, args, head)
+            line["zonal_mean"] = zonal_leg(sphx, torch, dev, args, head)
+            line["ragged_meshes"] = meshes_leg(sphx, torch, dev, args, head, pool)
+    pool.close()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def arcs_leg(sphx, torch, dev, args, flush) -> dict:
+def reduce_sum(value: int, device=None) -> int:
+    """Sum of an integer over all ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return int(value)
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def _flushed_times(torch, dev, flush, call, steps, warmup):
+    cur = torch.cuda.current_stream(dev)
+    evs = []
+    for i in range(warmup + steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        call(cur)
+        e1.record(cur)
+        if i >= warmup:
+            evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
+
+def stress_leg(sphx, torch, dev, args) -> dict:
+    """The 10^6-arc ill-conditioned workload (not the headline): each mode's
+    dense call timed with CUDA events, the L2 cache flushed (a 256 MiB write)
+    before each call."""
+    A, B, z = W.stress_arcs(STRESS_ARCS)
+    tA, tB, tz = (torch.from_numpy(v).to(dev) for v in (A, B, z))
+    pts = torch.empty((STRESS_ARCS, 2, 3), dtype=torch.float64, device=dev)
+    cnt = torch.empty((STRESS_ARCS,), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    res = {"workload": STRESS_WORKLOAD, "arcs": STRESS_ARCS,
+           "l2": "flushed between timed steps (256 MiB write)", "modes": {}}
+    for mode in MODES:
+        ms = _flushed_times(torch, dev, flush, lambda s, m=mode: sphx.sphx_intersect_gca_constlat(
+            tA, tB, tz, pts, cnt, m, s), args.steps, args.warmup)
+        hits = int(torch.clamp(cnt, min=0).sum().item())
+        res["modes"][mode] = {"ms_per_step": ms, "value": hits / (ms * 1e-3), "unit": UNIT,
+                              "arcs_per_s": STRESS_ARCS / (ms * 1e-3), "hits_per_step": hits,
+                              "hbm_frac": BYTES_PER_ARC * STRESS_ARCS / (ms * 1e-3) / 1e9
+                              / measured_hbm_peak()}
+    return res
+
+
+def arcs_leg(sphx, torch, dev, args) -> dict:
     """Arc x arc intersections (not the headline): 10^6 pairs of great circle
     arcs (50 % uniform, 15 % short, 15 % nearly parallel circles, 10 % crossings
     near an endpoint, 10 % misses), each mode timed with CUDA events over
     `steps` calls, the L2 cache flushed before each."""
     A1, A2, B1, B2 = W.arc_pairs(1_000_000)
     t = [torch.from_numpy(v).to(dev) for v in (A1, A2, B1, B2)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     n = len(A1)
     pts = torch.empty((n, 2, 3), dtype=torch.float64, device=dev)
     cnt = torch.empty(n, dtype=torch.int32, device=dev)
@@ -431,16 +593,18 @@ def arcs_leg(sphx, torch, dev, args, flush) -> dict:
     return res
 
 
-def adaptive_leg(sphx, torch, dev, args, flush, stress) -> dict:
+def adaptive_leg(sphx, torch, dev, args) -> dict:
     """The adaptive filter (not the headline): on the 10^6 stress arcs and on
     10^6 well-conditioned arcs (uniform endpoints, arc length uniform in
     (0, pi/2), one latitude inside each arc's z-range), the time per dense call
     of the adaptive mode beside the integer-limb and direct FP64 forms, and the
     share of arcs the filter hands on to the integer-limb form."""
     cur = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     res = {"workloads": {}}
     for name in ("stress", "uniform"):
-        A, B, z = stress if name == "stress" else W.uniform_arcs(N_ARCS, seed=W.DEFAULT_SEED + 5)
+        A, B, z = (W.stress_arcs(STRESS_ARCS) if name == "stress"
+                   else W.uniform_arcs(STRESS_ARCS, seed=W.DEFAULT_SEED + 5))
         tA, tB, tz = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (A, B, z))
         n = len(z)
         pts = torch.empty((n, 2, 3), dtype=torch.float64, device=dev)
@@ -654,61 +818,27 @@ def meshes_leg(sphx, torch, dev, args, head, pool) -> dict:
     return res
 
 
-def measured_hbm_peak() -> float:
+def measured_hbm_peak_src() -> tuple[float, str]:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
     except (OSError, KeyError, ValueError):
-        return 6800.0  # fallback figure of the profiling recipe
+        return 6800.0, "6.8 TB/s, the profiling recipe's fallback (of fallback)"
 
 
-def cpu_baseline_leg() -> dict:
-    """The exact oracle, as it stands, on all host cores over a bounded sample."""
-    import multiprocessing as mp
-    cores = os.cpu_count() or 1
-    n = min(N_ARCS, 6000 * cores)  # ~0.6 s of oracle work per core
-    A, B, z = W.stress_arcs(N_ARCS)
-    with mp.get_context("spawn").Pool(cores) as pool:
-        oracle_rate(A[:1024], B[:1024], z[:1024], pool)  # start the workers
-        rate = oracle_rate(A[:n], B[:n], z[:n], pool)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} arcs of the 10^6-arc stress workload",
-            "step_reference": step_reference_rates(A, B, z)}
+def measured_hbm_peak() -> float:
+    return measured_hbm_peak_src()[0]
 
 
-def step_reference_rates(A, B, z) -> dict:
-    """The paper's two FP64 forms as scalar C on one host core (the step
-    reference, gcc -O2 -ffp-contract=off): direct Eq. 2.2 and AccuX
-    (Algorithm 8), over the whole 10^6-arc stress workload. The paper reports
-    AccuX about 9x slower than the direct form serially (Sec. 8)."""
-    from oracle import steps
-    steps.lib()  # build outside the timing
-    out = {}
-    for name, fn in (("direct", lambda: steps.direct(A, B, z)),
-                     ("accux", lambda: steps.accux(A, B, z, variant=2))):
-        best = float("inf")
-        for _ in range(3):
-            t0 = time.perf_counter()
-            fn()
-            best = min(best, time.perf_counter() - t0)
-        out[name] = {"value": len(z) / best, "unit": UNIT, "cores": 1}
-    out["accux_over_direct_time"] = out["direct"]["value"] / out["accux"]["value"]
-    out["sample"] = "the whole 10^6-arc stress workload, one core, best of 3"
-    return out
-
-
-def e2e_leg(sphx, torch, dev, A, B, z, args, mode) -> dict:
-    """Same metric through the C ABI from pinned HOST buffers
+def e2e_leg(sphx, torch, dev, hA, hB, hz, args, mode) -> dict:
+    """Same metric through the C ABI from page-locked HOST buffers
     (sphx_intersect_gca_constlat_host): every step moves the inputs in and the
     points and counts out; with page-locked buffers the kernel reads and writes
     host memory in place, so the transfers overlap the arithmetic."""
-    n = len(z)
-    hA = torch.from_numpy(A).pin_memory()
-    hB = torch.from_numpy(B).pin_memory()
-    hz = torch.from_numpy(z).pin_memory()
-    hP = torch.empty((n, 2, 3), dtype=torch.float64).pin_memory()
-    hC = torch.empty((n,), dtype=torch.int32).pin_memory()
+    n = len(hz)
+    hP = torch.empty((n, 2, 3), dtype=torch.float64, pin_memory=True)
+    hC = torch.empty((n,), dtype=torch.int32, pin_memory=True)
     cur = torch.cuda.current_stream(dev)
     with sphx.Context(dev.index or 0) as ctx:
         for _ in range(args.warmup):
@@ -726,10 +856,13 @@ def e2e_leg(sphx, torch, dev, A, B, z, args, mode) -> dict:
     ms = e0.elapsed_time(e1) / args.steps
     ms = reduce_max(ms, dev)
     _, world, _ = dist_env()
-    return {"value": world * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    hits = int(np.clip(hC.numpy(), 0, None).sum())
+    del hP, hC
+    return {"value": None, "unit": UNIT, "ms_per_step": ms, "hits_per_step": hits,
+            "arcs_per_s": world * n / (ms * 1e-3),
             "h2d_bytes_per_step": n * 56, "d2h_bytes_per_step": n * 52,
-            "path": "sphx_intersect_gca_constlat_host, pinned host buffers (read and written "
-                    "in place by the kernel over NVLink-C2C)"}
+            "path": "sphx_intersect_gca_constlat_host, page-locked host buffers (read and "
+                    "written in place by the kernel over NVLink-C2C)"}
 
 
 if __name__ == "__main__":
