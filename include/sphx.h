@@ -355,12 +355,25 @@ sphx_status sphx_zonal_sums(sphx_context *ctx, const int32_t *band_lo, const int
    streams, other host threads) race on the array and must be serialised by
    the caller.
    A capacity overflow shows as *out_total > out_cap (only out_cap records
-   are written). */
+   are written). The kernels' other findings (a candidate latitude index
+   outside the batch, from corrupt offsets) are recorded in a status word in
+   the same array: sphx_noalloc_sync_status reads it. */
 sphx_status sphx_intersect_ragged_noalloc(const double *A, const double *B,
                                           const int64_t *edge_offsets, int32_t M, int64_t E,
                                           const double *lat_z, const int64_t *lat_offsets,
                                           int64_t L, sphx_mode mode, sphx_hit *out,
                                           int64_t out_cap, int64_t *out_total, sphx_stream stream);
+
+/* Device status of the allocation-free call (the paper has no counterpart).
+   Synchronises `stream`, reads the status word that the kernels of the last
+   sphx_intersect_ragged_noalloc call on the current device set, and clears
+   it. Returns SPHX_OK, SPHX_ERR_CAPACITY (more hits than out_cap) or
+   SPHX_ERR_INVALID_ARG (a candidate outside the batch, from inconsistent
+   offsets), or SPHX_ERR_CUDA. Allocates nothing. Each call of
+   sphx_intersect_ragged_noalloc clears the word first, so this reports the
+   latest call only; calls that overlap on the GPU race on it as on the rest
+   of the array. */
+sphx_status sphx_noalloc_sync_status(sphx_stream stream);
 
 /* Synchronise `stream`, read and clear the context's device status word.
    Returns SPHX_OK, SPHX_ERR_CAPACITY or SPHX_ERR_TIMEOUT (or SPHX_ERR_CUDA). */

@@ -57,20 +57,26 @@ struct RaggedScratch {
 
 // argument block of the persistent ragged kernel
 struct RaggedArgs {
-    const double *A, *B, *lat_z;
-    const int32_t *lo;
-    const long long *offsets;  // E + 1 entries: exclusive scan of candidate counts
-    int64_t E, L;
-    sphx_hit *out;
-    int64_t cap;
-    unsigned long long *out_total;
-    unsigned long long *counters;  // [0] chunk ticket
-    unsigned long long *ring;      // look-back ring (ORDERED)
-    int64_t ring_slots;            // power of two
-    unsigned *status;
-    int hold_first;                // failure injection (tests): chunk 0 never publishes its
+    const double *A = nullptr, *B = nullptr, *lat_z = nullptr;
+    const int32_t *lo = nullptr;
+    const long long *offsets = nullptr;  // E + 1 entries: exclusive scan of candidate counts
+    int64_t E = 0, L = 0;
+    sphx_hit *out = nullptr;
+    int64_t cap = 0;
+    unsigned long long *out_total = nullptr;
+    unsigned long long *counters = nullptr;  // [0] chunk ticket
+    unsigned long long *ring = nullptr;      // look-back ring (ORDERED)
+    int64_t ring_slots = 1;                  // power of two
+    unsigned *status = nullptr;
+    int hold_first = 0;            // failure injection (tests): chunk 0 never publishes its
                                    // prefix, so the look-back of chunk 1 waits out its limit
 };
+
+// exclusive scan of the candidate counts (ragged.cu): edges per scan block,
+// and the number of blocks (each writes one block sum) for E edges
+constexpr int kScanThreads = 256, kScanItems = 16;
+constexpr int64_t kScanTile = int64_t(kScanThreads) * kScanItems;
+constexpr int64_t scan_blocks_const(int64_t E) { return (E + kScanTile - 1) / kScanTile; }
 
 // ragged.cu
 int64_t scan_blocks_for(int64_t E);

@@ -21,8 +21,11 @@ namespace sphx {
 namespace {
 
 constexpr int64_t kNoAllocMaxEdges = SPHX_NOALLOC_MAX_EDGES;
-constexpr int64_t kScanTileEdges = 256 * 16;  // edges per scan block (ragged.cu)
-constexpr int64_t kMaxScanBlocks = (kNoAllocMaxEdges + kScanTileEdges - 1) / kScanTileEdges;
+// the scan writes one block sum per scan_blocks_const(E) block (plus the
+// total); its tile size is the one ragged.cu's scan kernels use (common.cuh)
+constexpr int64_t kMaxScanBlocks = scan_blocks_const(kNoAllocMaxEdges);
+static_assert(kMaxScanBlocks * kScanTile >= kNoAllocMaxEdges,
+              "block-sum area too small for the largest accepted batch");
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -103,7 +106,7 @@ extern "C" sphx_status sphx_intersect_ragged_noalloc(const double *A, const doub
     SPHX_CUDA(cudaMemsetAsync(out_total, 0, sizeof(int64_t), s));
     SPHX_CUDA(launch_candidates(A, B, edge_offsets, M, E, lat_z, L, lat_offsets, lo, hi, sms, s));
     SPHX_CUDA(launch_scan(lo, hi, E, block_sums, offsets, s));
-    RaggedArgs a;
+    RaggedArgs a{};
     a.A = A;
     a.B = B;
     a.lat_z = lat_z;
@@ -121,5 +124,21 @@ extern "C" sphx_status sphx_intersect_ragged_noalloc(const double *A, const doub
     RaggedShape sh;
     sh.compaction = SPHX_COMPACT_ATOMIC;
     SPHX_CUDA(launch_ragged((int)mode, sh, a, sms, s));
+    return SPHX_OK;
+}
+
+extern "C" sphx_status sphx_noalloc_sync_status(sphx_stream stream) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SPHX_CUDA(cudaStreamSynchronize(s));
+    unsigned char *base = nullptr;
+    int sms = 1;
+    sphx_status st = scratch_for_current(&base, &sms);
+    if (st != SPHX_OK) return st;
+    unsigned *status = reinterpret_cast<unsigned *>(base + kOffStatus);
+    unsigned h = 0;
+    SPHX_CUDA(cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost));
+    SPHX_CUDA(cudaMemset(status, 0, sizeof h));
+    if (h & (kStatusScratch | kStatusInvalid)) return SPHX_ERR_INVALID_ARG;
+    if (h & kStatusCapacity) return SPHX_ERR_CAPACITY;
     return SPHX_OK;
 }

@@ -67,7 +67,8 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
 }
 
 // ---- exclusive scan of (hi - lo) into int64 offsets[E + 1] ----------------------
-constexpr int kScanThreads = 256, kScanItems = 16, kScanTile = kScanThreads * kScanItems;
+// (kScanThreads, kScanItems and kScanTile are in common.cuh: the allocation-free
+// call sizes its fixed block-sum area from them)
 
 __device__ __forceinline__ long long count_of(const int32_t *lo, const int32_t *hi, int64_t e) {
     const int d = hi[e] - lo[e];
@@ -350,7 +351,7 @@ static RaggedKernelFn pick_kernel(int mode, int K, bool ordered) {
     }
 }
 
-int64_t scan_blocks_for(int64_t E) { return (E + kScanTile - 1) / kScanTile; }
+int64_t scan_blocks_for(int64_t E) { return scan_blocks_const(E); }
 
 cudaError_t launch_candidates(const double *A, const double *B, const int64_t *edge_offsets,
                               int M, int64_t E, const double *lat_z, int64_t L,

@@ -68,6 +68,7 @@ _SIGS = {
                                              ctypes.c_int, _vp, _i64, _vp, _vp]),
     "sphx_intersect_ragged_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i64, _vp, _vp, _i64,
                                                      ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "sphx_noalloc_sync_status": (ctypes.c_int, [_vp]),
     "sphx_band_ranges": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp,
                                         _vp, _vp]),
     "sphx_band_areas": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp,
@@ -349,6 +350,12 @@ def sphx_intersect_ragged_noalloc(A, B, edge_offsets, lat_z, lat_offsets, out, o
                                              _ptr(lat_z), _ptr(lat_offsets), L, _mode(mode),
                                              _ptr(out), cap, _ptr(out_total), _stream(stream))
     _check(st, "sphx_intersect_ragged_noalloc")
+
+
+def sphx_noalloc_sync_status(stream=None) -> int:
+    """Status of the latest allocation-free ragged call on the current device
+    (synchronises `stream`; clears the word): OK, ERR_CAPACITY or ERR_INVALID_ARG."""
+    return lib().sphx_noalloc_sync_status(_stream(stream))
 
 
 def sphx_autotune_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, out, out_total,

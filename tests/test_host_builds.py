@@ -63,7 +63,24 @@ def lib():
         f.argtypes = [u3, ctypes.c_int, ctypes.c_int, u3, ctypes.c_int, ctypes.c_int, u3, ip, ip]
     L.h_to_double.argtypes = [u3, ctypes.c_int, ctypes.c_int]
     L.h_to_double.restype = ctypes.c_double
+    L.h_check_seeds.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)]
+    L.h_check_seeds.restype = ctypes.c_uint64
     return L
+
+
+@pytest.mark.parametrize("which", ["rcp32", "rsqrt32"])
+def test_host_fp32_seeds_are_correctly_rounded(lib, which):
+    """The FP32 seeds of the integer-limb reciprocal and square root: the
+    host forms (through FP64) equal the correctly rounded value on every float
+    of one binade (two for the square root), so they equal the device's
+    correctly rounded __frcp_rn / __frsqrt_rn bit for bit. (The on-arc test's
+    normalisation factor, rsqrt_approx, is rsqrtf on the device and
+    1 / sqrtf on the host: that one factor may differ in its last bits, which
+    moves no decision outside the oracle's near-endpoint flag, so the host
+    builds are checked against the oracle there, not against the device.)"""
+    bad = ctypes.c_uint32()
+    n = lib.h_check_seeds(0 if which == "rcp32" else 1, ctypes.byref(bad))
+    assert n == 0, (n, hex(bad.value))
 
 
 def limbs(M):

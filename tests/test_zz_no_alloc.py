@@ -82,3 +82,19 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     st = L.sphx_intersect_ragged_noalloc(fake, fake, fake, 1, E, fake, fake, 10, 1, fake, 10,
                                          fake, None)
     assert st == sphx.ERR_INVALID_ARG
+
+
+def test_noalloc_status_reports_capacity_then_clears():
+    """The status readback of the allocation-free call: a call with room for
+    too few records reports SPHX_ERR_CAPACITY (and *out_total > out_cap); the
+    next call, with room enough, reports SPHX_OK."""
+    d, cap = _batch(13)
+    t, _ = _noalloc_c_abi(d, 8, "wide")
+    assert t > 8
+    L = sphx.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.sphx_noalloc_sync_status(s) == sphx.ERR_CAPACITY
+    assert L.sphx_noalloc_sync_status(s) == sphx.OK  # read and cleared
+    t2, _ = _noalloc_c_abi(d, cap, "wide")
+    assert t2 == t
+    assert L.sphx_noalloc_sync_status(s) == sphx.OK
