@@ -95,7 +95,10 @@ typedef enum {
 typedef enum {
     SPHX_COMPACT_AUTO = 0,    /* autotuned choice, else ATOMIC */
     SPHX_COMPACT_ATOMIC = 1,  /* one atomicAdd per warp: record order unspecified */
-    SPHX_COMPACT_ORDERED = 2  /* decoupled look-back: records in (edge, lat, root) order */
+    SPHX_COMPACT_ORDERED = 2, /* decoupled look-back: records in (edge, lat, root) order */
+    SPHX_COMPACT_FUSED = 3    /* one persistent kernel: candidate ranges, pair queue in shared
+                                 memory, evaluation and one atomicAdd per warp; no range, prefix
+                                 sum or scratch passes over HBM; record order unspecified */
 } sphx_compaction;
 
 typedef struct sphx_context sphx_context;

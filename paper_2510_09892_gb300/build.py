@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsphx.so")
-SOURCES = ["dense.cu", "adaptive.cu", "ragged.cu", "runtime.cu", "noalloc.cu", "arcs.cu", "areas.cu"]
+SOURCES = ["dense.cu", "adaptive.cu", "ragged.cu", "fused.cu", "runtime.cu", "noalloc.cu", "arcs.cu",
+           "areas.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "-I", os.path.join(ROOT, "include")]

@@ -72,6 +72,20 @@ struct RaggedArgs {
                                    // prefix, so the look-back of chunk 1 waits out its limit
 };
 
+// argument block of the fused ragged kernel (fused.cu)
+struct FusedArgs {
+    const double *A = nullptr, *B = nullptr, *lat_z = nullptr;
+    const int64_t *edge_offsets = nullptr, *lat_offsets = nullptr;
+    const int32_t *lo_in = nullptr, *hi_in = nullptr;  // caller's ranges, or null
+    int M = 0;
+    int64_t E = 0, L = 0;
+    sphx_hit *out = nullptr;
+    int64_t cap = 0;
+    unsigned long long *out_total = nullptr;
+    unsigned long long *counters = nullptr;  // [0] chunk ticket
+    unsigned *status = nullptr;
+};
+
 // exclusive scan of the candidate counts (ragged.cu): edges per scan block,
 // and the number of blocks (each writes one block sum) for E edges
 constexpr int kScanThreads = 256, kScanItems = 16;
@@ -88,6 +102,9 @@ cudaError_t launch_scan(const int32_t *lo, const int32_t *hi, int64_t E, long lo
                         long long *offsets, cudaStream_t s);
 cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, int sm_count,
                           cudaStream_t s);
+// fused.cu
+cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
+                         cudaStream_t s);
 
 // device staging of the host-buffer dense call: kHostSlots chunks in flight,
 // one stream each (copy in, kernel, copy out stay in order on a slot's

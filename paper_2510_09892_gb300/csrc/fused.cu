@@ -1,0 +1,266 @@
+// Ragged call in one persistent kernel (SPHX_COMPACT_FUSED): candidate
+// latitudes, pair enumeration and the per-pair evaluation of Eq. 2.2 (steps
+// a1, a11, a12 and a2-a10 of the hot path) without the intermediate ranges,
+// prefix sum and their passes over HBM.
+//
+// Each block claims chunks of NT consecutive edges from a global ticket
+// counter (dynamic load balance; edges with many candidates and edges with
+// none cost what they cost). For a chunk:
+//
+//  1. the chunk's mesh: when all its edges lie in one mesh whose latitude grid
+//     fits (kStageLats doubles, 23 KB), that grid is staged in shared memory,
+//     once per mesh change, and every latitude search and latitude read below
+//     goes to shared memory; other chunks read the grids in global memory;
+//  2. one thread per edge: the edge's height range (FP32 for unit endpoints,
+//     FP64 otherwise, widened) and two searches into its mesh's sorted
+//     latitudes give the candidate indices [lo, hi) (or the caller's ranges);
+//  3. a block scan of the counts hi - lo numbers the chunk's (edge, latitude)
+//     pairs; they are appended to a block-wide queue in shared memory
+//     ({edge, latitude index, z0}), each thread locating its pair's edge by a
+//     binary search of the scan;
+//  4. whenever the queue holds NT pairs, every thread evaluates one of them
+//     (intersect_pair, any mode) and the hits are compacted with one atomicAdd
+//     per warp (record order unspecified). Pairs left in the queue carry over
+//     to the next chunk; the last partial queue is evaluated at the end.
+//
+// So the evaluation, which is nearly all of the arithmetic, always runs on
+// full warps, however sparse the candidates are among the edges (about one
+// pair per five edges on a 0.09-degree cubed sphere against 0.25-degree
+// latitudes, hundreds per edge for coarse meshes on fine grids).
+#include "common.cuh"
+#include "intersect.cuh"
+#include "ranges.cuh"
+
+namespace sphx {
+
+constexpr int kStageLats = 2944;  // latitudes of one mesh staged in shared memory (23 KB)
+
+template <int NT>
+__device__ __forceinline__ long long block_inclusive_scan(long long v, long long *ws,
+                                                          long long &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < NW ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < NW; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) ws[lane] = w;
+    }
+    __syncthreads();
+    total = ws[NW - 1];
+    const long long before = warp > 0 ? ws[warp - 1] : 0;
+    __syncthreads();  // ws is reused by the next scan
+    return before + x;
+}
+
+// evaluate queue entries [0, n) (thread t takes entry t) and append the hits
+template <int Mode>
+__device__ __forceinline__ void eval_queue(const FusedArgs &a, int n, const long long *qe,
+                                           const int *qk, const double *qz) {
+    const int t = threadIdx.x, lane = t & 31;
+    if ((t & ~31) >= n) return;  // the whole warp is past the queue's end
+    PairOut res;
+    res.hit[0] = res.hit[1] = false;
+    long long e = 0;
+    int k = 0;
+    int h = 0;
+    if (t < n) {
+        e = qe[t];
+        k = qk[t];
+        const double z0 = qz[t];
+        const double x1[3] = {a.A[3 * e], a.A[3 * e + 1], a.A[3 * e + 2]};
+        const double x2[3] = {a.B[3 * e], a.B[3 * e + 1], a.B[3 * e + 2]};
+        intersect_pair<Mode>(x1, x2, z0, res);
+        h = (int)res.hit[0] + (int)res.hit[1];
+    }
+    int incl = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned long long total = (unsigned)__shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0 && total) {
+        base = atomicAdd(a.out_total, total);
+        if (base + total > (unsigned long long)a.cap) atomicOr(a.status, kStatusCapacity);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned long long idx = base + (unsigned long long)(incl - h);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (res.hit[r]) {
+            if (idx < (unsigned long long)a.cap) {
+                sphx_hit rec;
+                rec.edge = e;
+                rec.lat = k;
+                rec.root = r;
+                rec.x = res.px[r];
+                rec.y = res.py[r];
+                a.out[idx] = rec;
+            }
+            ++idx;
+        }
+    }
+}
+
+template <int Mode, int NT>
+__global__ void __launch_bounds__(NT) fused_kernel(FusedArgs a) {
+    __shared__ double s_lat[kStageLats];
+    __shared__ long long s_qe[NT];
+    __shared__ int s_qk[NT];
+    __shared__ double s_qz[NT];
+    __shared__ long long s_incl[NT];
+    __shared__ int s_lo[NT];
+    __shared__ long long s_ws[32];
+    __shared__ long long s_chunk;
+    __shared__ int s_m0, s_single;
+    __shared__ int s_staged;  // mesh whose grid s_lat holds (-1: none)
+
+    const int t = threadIdx.x;
+    const long long nchunks = (a.E + NT - 1) / NT;
+    if (t == 0) s_staged = -1;
+    int qn = 0;  // queue length (the same in every thread)
+    while (true) {
+        if (t == 0) {
+            const long long c = (long long)atomicAdd(a.counters, 1ull);
+            s_chunk = c;
+            if (c < nchunks) {
+                // the chunk's first mesh; it is the only one if the mesh
+                // extends past the chunk's last edge (offsets are not
+                // validated by the host: clamp what is derived from them)
+                const long long e0 = c * NT;
+                int m = (int)upper_bound_dev<int64_t>(a.edge_offsets, a.M + 1, e0) - 1;
+                m = m < 0 ? 0 : (m >= a.M ? a.M - 1 : m);
+                const long long e_last = min(e0 + NT, (long long)a.E) - 1;
+                s_m0 = m;
+                s_single = a.edge_offsets[m + 1] > e_last ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        const long long c = s_chunk;
+        if (c >= nchunks) break;
+        const long long e = c * NT + t;
+        const bool valid = e < a.E;
+        int m = s_m0;
+        const bool single = s_single != 0;
+        if (!single)
+            while (m < a.M - 1 && a.edge_offsets[m + 1] <= e) ++m;
+        long long ls = a.lat_offsets[m], le = a.lat_offsets[m + 1];
+        ls = ls < 0 ? 0 : (ls > a.L ? a.L : ls);
+        le = le < ls ? ls : (le > a.L ? a.L : le);
+        // stage the mesh's latitudes when the whole chunk is in one mesh
+        const bool staged = single && le - ls <= kStageLats && !a.lo_in;
+        if (staged && s_staged != m) {
+            __syncthreads();  // every thread has read s_staged
+            for (long long i = t; i < le - ls; i += NT) s_lat[i] = a.lat_z[ls + i];
+            if (t == 0) s_staged = m;
+            __syncthreads();
+        }
+        // candidate range of this thread's edge (absolute latitude indices)
+        int32_t lo = (int32_t)ls, hi = (int32_t)ls;
+        if (valid) {
+            if (a.lo_in) {
+                lo = a.lo_in[e];
+                hi = a.hi_in[e];
+            } else {
+                const double x1[3] = {a.A[3 * e], a.A[3 * e + 1], a.A[3 * e + 2]};
+                const double x2[3] = {a.B[3 * e], a.B[3 * e + 1], a.B[3 * e + 2]};
+                double zmin, zmax;
+                const bool finite = finite_bits(x1[0]) && finite_bits(x1[1]) &&
+                                    finite_bits(x1[2]) && finite_bits(x2[0]) &&
+                                    finite_bits(x2[1]) && finite_bits(x2[2]);
+                if (finite &&
+                    (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
+                    const double *lz = staged ? s_lat : a.lat_z + ls;
+                    const int64_t l = lower_bound_ord(lz, le - ls, ord64(zmin));
+                    lo = (int32_t)(ls + l);
+                    hi = (int32_t)(ls + upper_bound_ord_from(lz, le - ls, l, ord64(zmax)));
+                    if (hi < lo) hi = lo;
+                }
+            }
+        }
+        const long long cnt = valid && hi > lo ? (long long)(hi - lo) : 0;
+        long long total;
+        const long long incl = block_inclusive_scan<NT>(cnt, s_ws, total);
+        s_incl[t] = incl;
+        s_lo[t] = lo;
+        __syncthreads();
+        // append the chunk's pairs to the queue, evaluating every full queue
+        for (long long q = 0; q < total;) {
+            const int take = (int)min((long long)(NT - qn), total - q);
+            if (t < take) {
+                const long long p = q + t;
+                // the edge holding pair p: first i with s_incl[i] > p
+                int i0 = 0, i1 = NT - 1;
+                while (i0 < i1) {
+                    const int mid = (i0 + i1) >> 1;
+                    if (s_incl[mid] > p)
+                        i1 = mid;
+                    else
+                        i0 = mid + 1;
+                }
+                const long long excl = i0 > 0 ? s_incl[i0 - 1] : 0;
+                const long long k = (long long)s_lo[i0] + (p - excl);
+                double z0 = 2.0;  // beyond the poles: no candidate
+                int kk = (int)k;
+                if (k < 0 || k >= a.L) {  // corrupt caller ranges: skip the pair
+                    atomicOr(a.status, kStatusScratch);
+                    kk = -1;
+                } else {
+                    z0 = staged ? s_lat[k - ls] : a.lat_z[k];
+                }
+                s_qe[qn + t] = c * NT + i0;
+                s_qk[qn + t] = kk;
+                s_qz[qn + t] = z0;
+            }
+            qn += take;
+            q += take;
+            __syncthreads();
+            if (qn == NT) {
+                // entries whose latitude was out of range carry kk = -1 and
+                // z0 = 2, a height beyond the poles: s^2 < 0, no hit
+                eval_queue<Mode>(a, NT, s_qe, s_qk, s_qz);
+                qn = 0;
+                __syncthreads();
+            }
+        }
+    }
+    if (qn > 0) eval_queue<Mode>(a, qn, s_qe, s_qk, s_qz);
+}
+
+template <int Mode>
+static cudaError_t launch_mode(int threads, const FusedArgs &a, unsigned grid, cudaStream_t s) {
+    if (threads == 128) {
+        fused_kernel<Mode, 128><<<grid, 128, 0, s>>>(a);
+    } else {
+        fused_kernel<Mode, 256><<<grid, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
+                         cudaStream_t s) {
+    const int threads = sh.threads <= 128 ? 128 : 256;
+    const unsigned grid = (unsigned)(sm_count * sh.blocks_per_sm);
+    switch (mode) {
+        case kDirect: return launch_mode<kDirect>(threads, a, grid, s);
+        case kEftFp64: return launch_mode<kEftFp64>(threads, a, grid, s);
+        case kEftFf32: return launch_mode<kEftFf32>(threads, a, grid, s);
+        case kWideInt: return launch_mode<kWideInt>(threads, a, grid, s);
+        default: return launch_mode<kEftFp64Printed>(threads, a, grid, s);
+    }
+}
+
+}  // namespace sphx

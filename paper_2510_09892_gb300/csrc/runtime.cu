@@ -217,6 +217,28 @@ cudaError_t enqueue_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedS
     RaggedScratch &sc = ctx->scratch;
     const int32_t *lo = c.lo, *hi = c.hi;
     cudaError_t e;
+    if (sh.compaction == SPHX_COMPACT_FUSED) {
+        if ((e = cudaMemsetAsync(sc.counters, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(c.out_total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+        FusedArgs f;
+        f.A = c.A;
+        f.B = c.B;
+        f.lat_z = c.lat_z;
+        f.edge_offsets = c.edge_offsets;
+        f.lat_offsets = c.lat_offsets;
+        f.lo_in = c.lo;
+        f.hi_in = c.hi;
+        f.M = c.M;
+        f.E = c.E;
+        f.L = c.L;
+        f.out = c.out;
+        f.cap = c.cap;
+        f.out_total = reinterpret_cast<unsigned long long *>(c.out_total);
+        f.counters = sc.counters;
+        f.status = ctx->status;
+        return launch_fused(c.mode, sh, f, ctx->sm_count, s);
+    }
     if (!lo) {
         e = launch_candidates(c.A, c.B, c.edge_offsets, c.M, c.E, c.lat_z, c.L, c.lat_offsets, sc.lo,
                               sc.hi, ctx->sm_count, s);
@@ -570,7 +592,7 @@ sphx_status sphx_set_tuning(sphx_context *ctx, const sphx_tuning *t) {
             return SPHX_ERR_INVALID_ARG;
         sh.pairs_per_lane = t->pairs_per_lane;
     }
-    if (t->compaction < 0 || t->compaction > 2) return SPHX_ERR_INVALID_ARG;
+    if (t->compaction < 0 || t->compaction > 3) return SPHX_ERR_INVALID_ARG;
     sh.compaction = t->compaction;
     sh.use_graph = t->use_graph ? 1 : 0;
     if ((int64_t)ctx->sm_count * sh.blocks_per_sm * sh.threads > (int64_t)ctx->sm_count * 2048)
@@ -608,7 +630,7 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
     const int requested = ctx->shape.compaction;
     std::vector<int> comps;
     if (requested == SPHX_COMPACT_AUTO)
-        comps = {SPHX_COMPACT_ATOMIC, SPHX_COMPACT_ORDERED};
+        comps = {SPHX_COMPACT_ATOMIC, SPHX_COMPACT_ORDERED, SPHX_COMPACT_FUSED};
     else
         comps = {requested};
     cudaEvent_t e0, e1;
@@ -621,6 +643,8 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
             for (int bps : {2, 4, 8})
                 for (int K : {1, 2, 4}) {
                     if (threads * bps > 2048) continue;
+                    // the fused kernel evaluates one queued pair per thread
+                    if (comp == SPHX_COMPACT_FUSED && K != 1) continue;
                     RaggedShape sh;
                     sh.threads = threads;
                     sh.blocks_per_sm = bps;

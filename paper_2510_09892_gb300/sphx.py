@@ -25,7 +25,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPO
 MODES = {"direct": MODE_DIRECT_FP64, "eft": MODE_EFT_FP64, "ff32": MODE_EFT_FF32,
          "eft_printed": MODE_EFT_FP64_PRINTED, "wide": MODE_WIDE_INT, "adaptive": MODE_ADAPTIVE}
 # sphx_compaction
-COMPACT_AUTO, COMPACT_ATOMIC, COMPACT_ORDERED = range(3)
+COMPACT_AUTO, COMPACT_ATOMIC, COMPACT_ORDERED, COMPACT_FUSED = range(4)
 
 HIT_DTYPE = [("edge", "<i8"), ("lat", "<i4"), ("root", "<i4"), ("x", "<f8"), ("y", "<f8")]
 HIT_BYTES = 32

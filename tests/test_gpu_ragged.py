@@ -89,7 +89,8 @@ def small_batch(seed=3):
     return W.ragged_meshes(6, 40, 600, seed=seed, lat_min=180, lat_max=500)
 
 
-@pytest.mark.parametrize("compaction", [sphx.COMPACT_ATOMIC, sphx.COMPACT_ORDERED])
+@pytest.mark.parametrize("compaction", [sphx.COMPACT_ATOMIC, sphx.COMPACT_ORDERED,
+                                        sphx.COMPACT_FUSED])
 @pytest.mark.parametrize("mode", ["eft", "direct"])
 def test_small_meshes_equal_all_pairs_reference(ctx, mode, compaction):
     batch = small_batch()
@@ -110,11 +111,14 @@ def test_small_meshes_equal_all_pairs_reference(ctx, mode, compaction):
     ctx.reset_tuning()
 
 
+@pytest.mark.parametrize("compaction", [sphx.COMPACT_ATOMIC, sphx.COMPACT_FUSED])
 @pytest.mark.parametrize("mode", ["eft", "wide"])
-def test_small_meshes_against_exact_oracle(ctx, mode):
+def test_small_meshes_against_exact_oracle(ctx, mode, compaction):
     batch = W.ragged_meshes(4, 20, 120, seed=9, lat_min=180, lat_max=260)
     d = to_dev(batch)
+    ctx.set_tuning(compaction=compaction)
     st, total, recs = run_ragged(ctx, d, mode)
+    ctx.reset_tuning()
     assert st == sphx.OK
     want, flagged, degenerate = oracle_ragged.intersect_ragged(
         batch["A"], batch["B"], batch["edge_offsets"], batch["lat_z"], batch["lat_offsets"])
@@ -135,6 +139,76 @@ def test_small_meshes_against_exact_oracle(ctx, mode):
         pts = np.array([[[got[key][0], got[key][1], z0]] * 2])
         _, _, gate = P.component_errors(pts, ref, np.array([z0]))
         assert gate.max() <= 4.0, (key, gate)
+
+
+def fused_batches(kind):
+    """Batches that take each path of the fused kernel: one mesh whose grid is
+    staged in shared memory (cubed sphere, 721 latitudes); many small meshes,
+    so that chunks of edges span mesh boundaries (grids read in global memory);
+    grids larger than the staging area (3000-3500 latitudes); an empty mesh in
+    the middle; a single edge."""
+    if kind == "cubed":
+        A, B = W.cubed_sphere_edges(12)
+        return {"A": A, "B": B, "edge_offsets": np.array([0, len(A)], dtype=np.int64),
+                "lat_z": W.latlon_latitudes(721), "lat_offsets": np.array([0, 721], dtype=np.int64)}
+    if kind == "tiny_meshes":
+        return W.ragged_meshes(40, 3, 30, seed=21, lat_min=180, lat_max=400)
+    if kind == "big_grids":
+        return W.ragged_meshes(3, 200, 700, seed=22, lat_min=3000, lat_max=3500)
+    if kind == "empty_mesh":
+        b = W.ragged_meshes(4, 100, 400, seed=23, lat_min=180, lat_max=300)
+        eo, lo_ = b["edge_offsets"], b["lat_offsets"]
+        b["edge_offsets"] = np.concatenate([eo[:3], eo[2:3], eo[3:]])
+        b["lat_offsets"] = np.concatenate([lo_[:3], lo_[2:3], lo_[3:]])
+        return b
+    A, B = W.cubed_sphere_edges(2)
+    return {"A": A[:1], "B": B[:1], "edge_offsets": np.array([0, 1], dtype=np.int64),
+            "lat_z": W.latlon_latitudes(181), "lat_offsets": np.array([0, 181], dtype=np.int64)}
+
+
+@pytest.mark.parametrize("threads,bps", [(128, 4), (256, 2)])
+@pytest.mark.parametrize("kind", ["cubed", "tiny_meshes", "big_grids", "empty_mesh", "one_edge"])
+@pytest.mark.parametrize("mode", ["eft", "direct"])
+def test_fused_kernel_equals_all_pairs_reference(ctx, mode, kind, threads, bps):
+    """The fused ragged kernel (ranges, pair queue and evaluation in one
+    launch): the same records as brute force over every (edge, latitude) pair
+    with the step reference, bit for bit, on every path of the kernel."""
+    batch = fused_batches(kind)
+    d = to_dev(batch)
+    ctx.set_tuning(threads_per_block=threads, blocks_per_sm=bps,
+                   compaction=sphx.COMPACT_FUSED, use_graph=1)
+    st, total, recs = run_ragged(ctx, d, mode)
+    ctx.reset_tuning()
+    assert st == sphx.OK
+    key, x, y = all_pairs_reference(batch, mode)
+    got, gx, gy = sorted_records(recs)
+    assert total == len(key) and np.array_equal(got, key)
+    assert P.same_bits(gx, x) and P.same_bits(gy, y)
+
+
+def test_fused_capacity_overflow_and_caller_ranges(ctx):
+    """The fused kernel: a buffer with room for a third of the hits gets
+    exactly its capacity of valid records, the status reports the overflow
+    and *out_total the full count; caller-given ranges are used as given."""
+    batch = small_batch(seed=24)
+    d = to_dev(batch)
+    key, x, y = all_pairs_reference(batch)
+    ctx.set_tuning(compaction=sphx.COMPACT_FUSED)
+    cap = len(key) // 3
+    st, total, recs = run_ragged(ctx, d, "eft", cap=cap)
+    assert st == sphx.ERR_CAPACITY and total == len(key) and len(recs) == cap
+    kk = {tuple(r) for r in key.tolist()}
+    assert all((int(r["edge"]), int(r["lat"]), int(r["root"])) in kk for r in recs)
+    assert ctx.sync_status() == sphx.OK
+    E = len(batch["A"])
+    eo, lo_ = batch["edge_offsets"], batch["lat_offsets"]
+    mesh_of = np.searchsorted(eo, np.arange(E), side="right") - 1
+    full_lo = torch.from_numpy(lo_[mesh_of].astype(np.int32)).to(DEV)
+    full_hi = torch.from_numpy(lo_[mesh_of + 1].astype(np.int32)).to(DEV)
+    st, total, recs = run_ragged(ctx, d, "eft", lo=full_lo, hi=full_hi)
+    ctx.reset_tuning()
+    got, gx, gy = sorted_records(recs)
+    assert st == sphx.OK and np.array_equal(got, key) and P.same_bits(gx, x)
 
 
 def test_cubed_sphere_with_latlon_grid(ctx):
