@@ -93,7 +93,7 @@ typedef enum {
 
 /* Output compaction scheme of the ragged call. */
 typedef enum {
-    SPHX_COMPACT_AUTO = 0,    /* autotuned choice, else ATOMIC */
+    SPHX_COMPACT_AUTO = 0,    /* autotuned choice among FUSED and ATOMIC, else FUSED */
     SPHX_COMPACT_ATOMIC = 1,  /* one atomicAdd per warp: record order unspecified */
     SPHX_COMPACT_ORDERED = 2, /* decoupled look-back: records in (edge, lat, root) order */
     SPHX_COMPACT_FUSED = 3    /* one persistent kernel: candidate ranges, pair queue in shared

@@ -34,10 +34,10 @@ void set_cuda_error(cudaError_t e);
 
 // launch shape of the ragged intersection kernel
 struct RaggedShape {  // defaults: what the autotuner picks on both GB300 workloads
-    int threads = 256;
+    int threads = 128;
     int blocks_per_sm = 8;
     int pairs_per_lane = 1;
-    int compaction = SPHX_COMPACT_ATOMIC;
+    int compaction = SPHX_COMPACT_FUSED;
     int use_graph = 1;
     bool operator<(const RaggedShape &o) const {
         return std::tie(threads, blocks_per_sm, pairs_per_lane, compaction, use_graph) <

@@ -31,8 +31,10 @@ constexpr int kAdaptive = 5;
 // few bytes of spills): with its square root and reciprocal on the integer
 // pipe it is bound by instruction issue, and the extra warps hide more of the
 // carry chains' latency (1-1.5 % on GB300 against 6 blocks at 80 registers).
+// The float-float mode shares its integer-limb core and asks for 6 (80
+// registers, no spills, against 107 and 4 blocks unbounded).
 template <int Mode>
-__global__ void __launch_bounds__(kTile, Mode == kWideInt ? 7 : 1)
+__global__ void __launch_bounds__(kTile, Mode == kWideInt ? 7 : (Mode == kEftFf32 ? 6 : 1))
     dense_kernel(const double *__restrict__ A, const double *__restrict__ B,
                  const double *__restrict__ Z, int64_t n, double *__restrict__ out_pts,
                  int32_t *__restrict__ out_count, unsigned long long *fallback, double gate) {

@@ -96,23 +96,24 @@ SPHX_HD F2 rcp2(F2 b) {
     return fast_two_sum(r0, mul(r0, e));
 }
 
-// a double as hi + lo (hi: its top 24 mantissa bits, lo: the next 24), by its
-// bits, for |x| in [2^-100, 2^100] or 0 (lo is 0 below the float range)
-SPHX_HD F2 split(double x) {
-    const uint64_t b = wide::bits_of(x);
-    const uint32_t h32 = (uint32_t)(b >> 32);
-    const int ex = (int)((h32 >> 20) & 0x7ffu);
-    if (ex < 1023 - 126) return {0.0f, 0.0f};
-    const uint32_t sign = h32 & 0x80000000u;
-    const float hi =
-        wide::float_of(sign | ((uint32_t)(ex - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
-    const uint32_t R = (uint32_t)b & 0x1fffffffu;  // the 29 bits below hi
-    if (R == 0u) return {hi, 0.0f};
-    const int c = wide::clz32(R) - 3;  // R = 1.f 2^(28 - c)
-    const int fe = ex - 1023 - 52 + (28 - c) + 127;
-    const float lo =
-        fe > 0 ? wide::float_of(sign | ((uint32_t)fe << 23) | (((R << c) >> 5) & 0x7fffffu)) : 0.0f;
-    return {hi, lo};
+// value(a) 2^-sc as hi + lo, for an integer-limb value a (K >= 2): hi holds
+// the top 24 mantissa bits, lo the next 24 rounded to nearest, so the pair is
+// within 2^-49 relative of the value. 0 when the value is below 2^-125 (the
+// callers' values are at most 2 in magnitude).
+template <int K>
+SPHX_HD F2 ff_of(const wide::W<K> &a, int sc) {
+    if (wide::is_zero(a)) return {0.0f, 0.0f};
+    const uint32_t top = a.m[K - 1], nxt = a.m[K - 2];
+    const int eh = a.e - sc;  // value = 0.M 2^eh, in [2^(eh-1), 2^eh)
+    if (eh - 1 + 127 <= 1 || eh - 1 + 127 >= 255) return {0.0f, 0.0f};
+    const uint32_t sign = a.neg << 31;
+    const float hi = wide::float_of(sign | ((uint32_t)(eh - 1 + 127) << 23) | ((top >> 8) & 0x7fffffu));
+    // the next 24 bits, rounded on the bit below them: L 2^(eh - 48), L <= 2^24
+    const uint32_t L = (((top & 0xffu) << 16) | (nxt >> 16)) + ((nxt >> 15) & 1u);
+    const int le = eh - 48 + 127;  // exponent field of 2^(eh - 48)
+    if (L == 0u || le <= 0) return {hi, 0.0f};
+    const float lo = mul(wide::f32_of_u32(L), wide::float_of((uint32_t)le << 23));
+    return fast_two_sum(hi, a.neg ? -lo : lo);
 }
 
 // a normal or zero float as a double (exact), by its bits

@@ -235,38 +235,68 @@ SPHX_HD double f64_of_f32_scaled(float f, int sc) {
     return wide::double_of(((uint64_t)(fe - 127 + 1023 - sc) << 52) | ((uint64_t)(b & 0x7fffffu) << 29));
 }
 
-SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
-                                          PairOut &o) {
+// The exact and 128-bit part of the integer-limb evaluation: n, |n_xy|^2 and
+// s^2 = |n_xy|^2 - |n|^2 z0^2, the quantities whose cancellation the paper's
+// error analysis is about. Returns false after filling `o` for the cases that
+// end here (non-finite input, degenerate arc, no candidate).
+struct WideCore {
+    wide::W<4> n[3], S2, s2;
+    bool tangent;
+};
+
+SPHX_HD bool wide_core(const double (&x1)[3], const double (&x2)[3], double z0, WideCore &c,
+                       PairOut &o) {
     using namespace wide;
     if (!(finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) && finite_bits(x2[0]) &&
-          finite_bits(x2[1]) && finite_bits(x2[2]) && finite_bits(z0)))
-        return clear(o, 0);
+          finite_bits(x2[1]) && finite_bits(x2[2]) && finite_bits(z0))) {
+        clear(o, 0);
+        return false;
+    }
     W<2> a[3], b[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         a[i] = from_double<2>(x1[i]);
         b[i] = from_double<2>(x2[i]);
     }
-    W<4> n[3];
-    n[0] = sub<4>(mul_exact(a[1], b[2]), mul_exact(a[2], b[1]));  // y1 z2 - z1 y2
-    n[1] = sub<4>(mul_exact(a[2], b[0]), mul_exact(a[0], b[2]));  // z1 x2 - x1 z2
-    n[2] = sub<4>(mul_exact(a[0], b[1]), mul_exact(a[1], b[0]));  // x1 y2 - y1 x2
-    if (is_zero(n[0]) && is_zero(n[1]) && is_zero(n[2])) return clear(o, -1);
+    c.n[0] = sub<4>(mul_exact(a[1], b[2]), mul_exact(a[2], b[1]));  // y1 z2 - z1 y2
+    c.n[1] = sub<4>(mul_exact(a[2], b[0]), mul_exact(a[0], b[2]));  // z1 x2 - x1 z2
+    c.n[2] = sub<4>(mul_exact(a[0], b[1]), mul_exact(a[1], b[0]));  // x1 y2 - y1 x2
+    if (is_zero(c.n[0]) && is_zero(c.n[1]) && is_zero(c.n[2])) {
+        clear(o, -1);
+        return false;
+    }
     const bool z0_zero = (bits_of(z0) << 1) == 0;
-    if (is_zero(n[0]) && is_zero(n[1])) return clear(o, z0_zero ? -1 : 0);
-    const W<4> S2 = add_same<4>(sqr<4>(n[0]), sqr<4>(n[1]));
-    const W<4> S3 = add_same<4>(S2, sqr<4>(n[2]));
+    if (is_zero(c.n[0]) && is_zero(c.n[1])) {
+        clear(o, z0_zero ? -1 : 0);
+        return false;
+    }
+    c.S2 = add_same<4>(sqr<4>(c.n[0]), sqr<4>(c.n[1]));
+    const W<4> S3 = add_same<4>(c.S2, sqr<4>(c.n[2]));
     const W<2> zz = from_double<2>(z0);
-    const W<4> s2 = sub<4>(S2, mul<4>(S3, mul_exact(zz, zz)));
-    if (s2.neg && !is_zero(s2)) return clear(o, 0);
-    const bool tangent = is_zero(s2);
+    c.s2 = sub<4>(c.S2, mul<4>(S3, mul_exact(zz, zz)));
+    if (c.s2.neg && !is_zero(c.s2)) {
+        clear(o, 0);
+        return false;
+    }
+    c.tangent = is_zero(c.s2);
+    return true;
+}
 
-    // on-arc test set-up (FP32 normals and endpoints, scaled by powers of two),
-    // placed before the root computation so that its latency overlaps that work
-    int emax = n[0].e;
-    emax = n[1].e > emax ? n[1].e : emax;
-    emax = n[2].e > emax ? n[2].e : emax;
-    const float nf[3] = {f32_rel(n[0], emax), f32_rel(n[1], emax), f32_rel(n[2], emax)};
+// Set-up of the on-arc test (FP32 normals and endpoints, scaled by powers of
+// two), placed before the root computation so that its latency overlaps that
+// work.
+struct OnArc {
+    float p1[3], p2[3], m1[3], m2[3], zf;
+    double inv1, inv2;
+};
+
+SPHX_HD void onarc_setup(const double (&x1)[3], const double (&x2)[3], double z0,
+                         const WideCore &c, OnArc &q) {
+    using namespace wide;
+    int emax = c.n[0].e;
+    emax = c.n[1].e > emax ? c.n[1].e : emax;
+    emax = c.n[2].e > emax ? c.n[2].e : emax;
+    const float nf[3] = {f32_rel(c.n[0], emax), f32_rel(c.n[1], emax), f32_rel(c.n[2], emax)};
     int sc1 = exponent_bits(x1[0]), sc2 = exponent_bits(x2[0]);
 #pragma unroll
     for (int i = 1; i < 3; ++i) {
@@ -274,38 +304,66 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
         sc1 = e1 > sc1 ? e1 : sc1;
         sc2 = e2 > sc2 ? e2 : sc2;
     }
-    float p1[3], p2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        p1[i] = f32_scaled(x1[i], sc1);
-        p2[i] = f32_scaled(x2[i], sc2);
+        q.p1[i] = f32_scaled(x1[i], sc1);
+        q.p2[i] = f32_scaled(x2[i], sc2);
     }
-    const float m1[3] = {wide::fma32(nf[1], p1[2], -nf[2] * p1[1]), wide::fma32(nf[2], p1[0], -nf[0] * p1[2]),
-                         wide::fma32(nf[0], p1[1], -nf[1] * p1[0])};
-    const float m2[3] = {wide::fma32(p2[1], nf[2], -p2[2] * nf[1]), wide::fma32(p2[2], nf[0], -p2[0] * nf[2]),
-                         wide::fma32(p2[0], nf[1], -p2[1] * nf[0])};
+    const float *p1 = q.p1, *p2 = q.p2;
+    q.m1[0] = wide::fma32(nf[1], p1[2], -nf[2] * p1[1]);
+    q.m1[1] = wide::fma32(nf[2], p1[0], -nf[0] * p1[2]);
+    q.m1[2] = wide::fma32(nf[0], p1[1], -nf[1] * p1[0]);
+    q.m2[0] = wide::fma32(p2[1], nf[2], -p2[2] * nf[1]);
+    q.m2[1] = wide::fma32(p2[2], nf[0], -p2[0] * nf[2]);
+    q.m2[2] = wide::fma32(p2[0], nf[1], -p2[1] * nf[0]);
     // l = 1 / |x| in FP32, except that endpoints of unit norm (to FP32
     // resolution) take l = 1 exactly: then d = P -+ x is exact near x
     const float r1 = wide::rsqrt_approx(p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]);
     const float r2 = wide::rsqrt_approx(p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]);
     const bool unit1 = (sc1 == -1 || sc1 == 0) && fabsf(r1 * (sc1 ? 2.0f : 1.0f) - 1.0f) < 1e-6f;
     const bool unit2 = (sc2 == -1 || sc2 == 0) && fabsf(r2 * (sc2 ? 2.0f : 1.0f) - 1.0f) < 1e-6f;
-    const double inv1 = unit1 ? 1.0 : f64_of_f32_scaled(r1, sc1);
-    const double inv2 = unit2 ? 1.0 : f64_of_f32_scaled(r2, sc2);
-    const float zf = f32_scaled(z0, 0);
+    q.inv1 = unit1 ? 1.0 : f64_of_f32_scaled(r1, sc1);
+    q.inv2 = unit2 ? 1.0 : f64_of_f32_scaled(r2, sc2);
+    q.zf = f32_scaled(z0, 0);
+}
+
+// the on-arc decision for the candidate (Px, Py, z0)
+SPHX_HD bool onarc_test(const double (&x1)[3], const double (&x2)[3], double z0, const OnArc &q,
+                        double Px, double Py) {
+    const float pf[3] = {f32_scaled(Px, 0), f32_scaled(Py, 0), q.zf};
+    const double l1 = (pf[0] * q.p1[0] + pf[1] * q.p1[1] + pf[2] * q.p1[2] >= 0.0f) ? q.inv1 : -q.inv1;
+    const double l2 = (pf[0] * q.p2[0] + pf[1] * q.p2[1] + pf[2] * q.p2[2] >= 0.0f) ? q.inv2 : -q.inv2;
+    const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0),
+                         f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
+                         f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
+    const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0),
+                         f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
+                         f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
+    const float t1 = wide::fma32(d1[0], q.m1[0], wide::fma32(d1[1], q.m1[1], d1[2] * q.m1[2]));
+    const float t2 = wide::fma32(d2[0], q.m2[0], wide::fma32(d2[1], q.m2[1], d2[2] * q.m2[2]));
+    return t1 >= 0.0f && t2 >= 0.0f;
+}
+
+SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
+                                          PairOut &o) {
+    using namespace wide;
+    WideCore c;
+    if (!wide_core(x1, x2, z0, c, o)) return;
+    OnArc q;
+    onarc_setup(x1, x2, z0, c, q);
     // P_xy = g n_xy + sigma h (n_y, -n_x) with g = -z0 n_z / |n_xy|^2 and
     // h = -s / |n_xy|^2: Eq. 2.2 with the division distributed
-    const W<3> nx = narrow<4, 3>(n[0]), ny = narrow<4, 3>(n[1]), nz = narrow<4, 3>(n[2]);
-    const W<3> rS2 = negate<3>(recip_int<3>(narrow<4, 3>(S2)));  // -1 / |n_xy|^2
+    const W<3> nx = narrow<4, 3>(c.n[0]), ny = narrow<4, 3>(c.n[1]), nz = narrow<4, 3>(c.n[2]);
+    const W<3> rS2 = negate<3>(recip_int<3>(narrow<4, 3>(c.S2)));  // -1 / |n_xy|^2
     const W<3> g = mul<3>(mul<3>(from_double<3>(z0), nz), rS2);
-    const W<3> h = tangent ? zero<3>() : mul<3>(sqrt_int<3>(narrow<4, 3>(s2)), rS2);
+    const W<3> h = c.tangent ? zero<3>() : mul<3>(sqrt_int<3>(narrow<4, 3>(c.s2)), rS2);
     const W<3> gx = mul<3>(g, nx), gy = mul<3>(g, ny);
     const W<3> hx = mul<3>(h, nx), hy = mul<3>(h, ny);
     W<3> Px_lin[2], Py_lin[2];  // both roots: g n_x +- h n_y and g n_y -+ h n_x
     add_sub<3>(gx, hy, Px_lin[0], Px_lin[1]);
     add_sub<3>(gy, hx, Py_lin[1], Py_lin[0]);
 
-    const int nroots = tangent ? 1 : 2;
+    const int nroots = c.tangent ? 1 : 2;
     o.count = 0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -315,126 +373,65 @@ SPHX_HD void pair_wide(const double (&x1)[3], const double (&x2)[3], double z0,
         const double Py = to_double<3>(Py_lin[r]);
         o.px[r] = Px;
         o.py[r] = Py;
-        const float pf[3] = {f32_scaled(Px, 0), f32_scaled(Py, 0), zf};
-        const double l1 = (pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f) ? inv1 : -inv1;
-        const double l2 = (pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f) ? inv2 : -inv2;
-        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0),
-                             f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
-                             f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
-        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0),
-                             f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
-                             f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
-        const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
-        const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));
-        if (t1 >= 0.0f && t2 >= 0.0f) {
+        if (onarc_test(x1, x2, z0, q, Px, Py)) {
             o.hit[r] = true;
             ++o.count;
         }
     }
 }
 
-// ---- float-float, FP64 only where stability needs it ---------------------------
-// For endpoints of unit norm. The cross product of nearly coincident or nearly
-// antipodal endpoints cancels: d = x2 - x1 (or x2 + x1 when x1 . x2 < 0) is
-// formed in FP64 (one subtraction per component, exact or one rounding) and
-// n = x1 x d = x1 x x2 in float-float, where it is well-conditioned (d makes
-// an angle of at least 45 degrees with x1). |n_xy|^2, |n|^2, s^2, the square
-// root, 1 / |n_xy|^2 and P = g n_xy +- h (n_y, -n_x) (g = -z0 n_z / |n_xy|^2,
-// h = -s / |n_xy|^2, Eq. 2.2) follow in float-float on the FP32 pipe; the
-// on-arc test is that of pair_wide with l = +-1. s^2 carries about 46 bits,
-// so accuracy degrades near tangency and near the poles like that of any
-// fixed-precision evaluation of Eq. 2.2 (stated bound in the header). Other
-// endpoints go to pair_wide.
-
-// x 2^k for a finite double, by its bits (0 when the result leaves the normal range)
-SPHX_HD double scale_pow2(double x, int k) {
-    const uint64_t b = wide::bits_of(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex == 0 || ex + k <= 0) return 0.0;
-    return wide::double_of(b + ((uint64_t)(int64_t)k << 52));
-}
-
-SPHX_HD void pair_ff2(const double (&x1)[3], const double (&x2)[3], double z0, PairOut &o) {
+// ---- float-float tail on the exact core --------------------------------------
+// The cancelling steps stay exact or 128-bit on the integer limbs (wide_core:
+// the cross product of nearly coincident or nearly antipodal endpoints and
+// s^2 = |n_xy|^2 - |n|^2 z0^2, whose sign decides whether the circles meet);
+// everything after them runs in float-float on the FP32 pipe: with F the
+// exponent of the larger of |n_x|, |n_y|, the quantities b = n_xy 2^-F,
+// T = |n_xy|^2 2^-2F in [1/4, 2), sigma = s^2 2^-2F <= T and Z = z0 n_z 2^-F
+// (|Z| <= sqrt(T) whenever s^2 >= 0) are rounded to pairs (2^-49), and
+//
+//     P_x = G b_x +- H b_y,  P_y = G b_y -+ H b_x,
+//     G = -Z / T,  H = -sqrt(sigma) / T
+//
+// (Eq. 2.2: g n_x = G b_x with g = -z0 n_z / |n_xy|^2, h n_y = H b_y with
+// h = -s / |n_xy|^2). With eps = 2^-48 and the pair operations' relative
+// errors (products <= 3 eps, reciprocal and square root <= 3 eps, sums of
+// pairs <= 2 eps of the operands' magnitudes), each term G b and H b is within
+// 13 eps of its value and each coordinate within 15 eps (|g n_x| + |h n_y|),
+// so |dP| <= 15 eps sqrt(2) sqrt(1 - z0^2) < 2^-44 sqrt(1 - z0^2) (the terms
+// are bounded by sqrt(1 - z0^2), |g n_xy|^2 + |h n_xy|^2 = 1 - z0^2). The
+// hit count follows the exact sign of s^2 and the on-arc test of pair_wide
+// (P within 2^-44 moves no decision outside the oracle's 2^-40 endpoint
+// flag).
+SPHX_HD void pair_ff32(const double (&x1)[3], const double (&x2)[3], double z0, PairOut &o) {
+    using namespace wide;
     using namespace ffa;
-    if (!(finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) && finite_bits(x2[0]) &&
-          finite_bits(x2[1]) && finite_bits(x2[2]) && finite_bits(z0)))
-        return clear(o, 0);
-    float p1[3], p2[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        p1[i] = f32_scaled(x1[i], 0);
-        p2[i] = f32_scaled(x2[i], 0);
-    }
-    const float q1 = wide::fma32(p1[0], p1[0], wide::fma32(p1[1], p1[1], p1[2] * p1[2]));
-    const float q2 = wide::fma32(p2[0], p2[0], wide::fma32(p2[1], p2[1], p2[2] * p2[2]));
-    if (!(fabsf(q1 - 1.0f) < 1e-6f && fabsf(q2 - 1.0f) < 1e-6f)) return pair_wide(x1, x2, z0, o);
-    const bool same = p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f;
-    // one FMA per component with a +-1 factor (a select between x2 - x1 and
-    // x2 + x1 would evaluate both on the FP64 pipe)
-    const double sg = same ? 1.0 : -1.0;
-    double d[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = wide::fma64(-sg, x1[i], x2[i]);
-    int E = exponent_bits(d[0]);
-    E = exponent_bits(d[1]) > E ? exponent_bits(d[1]) : E;
-    E = exponent_bits(d[2]) > E ? exponent_bits(d[2]) : E;
-    if (E < -1022) return clear(o, -1);  // d = 0: x2 = +-x1, n = 0
-    F2 X[3], D[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        X[i] = split(x1[i]);
-        D[i] = split(scale_pow2(d[i], -E));  // max |d_i| in [1, 2)
-    }
-    const F2 nx = add2(mul2(X[1], D[2]), neg(mul2(X[2], D[1])));
-    const F2 ny = add2(mul2(X[2], D[0]), neg(mul2(X[0], D[2])));
-    const F2 nz = add2(mul2(X[0], D[1]), neg(mul2(X[1], D[0])));
-    if (nx.hi == 0.0f && ny.hi == 0.0f && nz.hi == 0.0f) return clear(o, -1);
-    const bool z0_zero = (wide::bits_of(z0) << 1) == 0;
-    if (nx.hi == 0.0f && ny.hi == 0.0f) return clear(o, z0_zero ? -1 : 0);
-    const F2 S2 = add2(sqr2(nx), sqr2(ny));
-    const F2 S3 = add2(S2, sqr2(nz));
-    const F2 Z = split(z0);
-    const F2 s2 = add2(S2, neg(mul2(S3, sqr2(Z))));
-    if (s2.hi < 0.0f) return clear(o, 0);
-    const bool tangent = s2.hi == 0.0f;
-    const F2 r = neg(rcp2(S2));  // -1 / |n_xy|^2
-    const F2 g = mul2(mul2(Z, nz), r);
-    const F2 h = tangent ? F2{0.0f, 0.0f} : mul2(sqrt2(s2), r);
-    const F2 gx = mul2(g, nx), gy = mul2(g, ny), hx = mul2(h, nx), hy = mul2(h, ny);
-
-    // on-arc test (as in pair_wide, endpoints of unit norm: l = +-1)
-    const float nf[3] = {nx.hi, ny.hi, nz.hi};
-    const float m1[3] = {wide::fma32(nf[1], p1[2], -nf[2] * p1[1]), wide::fma32(nf[2], p1[0], -nf[0] * p1[2]),
-                         wide::fma32(nf[0], p1[1], -nf[1] * p1[0])};
-    const float m2[3] = {wide::fma32(p2[1], nf[2], -p2[2] * nf[1]), wide::fma32(p2[2], nf[0], -p2[0] * nf[2]),
-                         wide::fma32(p2[0], nf[1], -p2[1] * nf[0])};
-    const float zf = f32_scaled(z0, 0);
-    const int nroots = tangent ? 1 : 2;
+    WideCore c;
+    if (!wide_core(x1, x2, z0, c, o)) return;
+    OnArc q;
+    onarc_setup(x1, x2, z0, c, q);
+    const int F = c.n[0].e > c.n[1].e ? c.n[0].e : c.n[1].e;
+    const F2 bx = ff_of<4>(c.n[0], F), by = ff_of<4>(c.n[1], F);
+    const F2 T = ff_of<4>(c.S2, 2 * F);
+    const F2 sig = c.tangent ? F2{0.0f, 0.0f} : ff_of<4>(c.s2, 2 * F);
+    const F2 Z = ff_of<3>(mul<3>(from_double<3>(z0), narrow<4, 3>(c.n[2])), F);
+    const F2 iT = rcp2(T);
+    const F2 G = neg(mul2(Z, iT));
+    const F2 H = neg(mul2(sqrt2(sig), iT));
+    const F2 gx = mul2(G, bx), gy = mul2(G, by), hx = mul2(H, bx), hy = mul2(H, by);
+    const int nroots = c.tangent ? 1 : 2;
     o.count = 0;
 #pragma unroll
-    for (int rt = 0; rt < 2; ++rt) {
-        o.hit[rt] = false;
-        if (rt >= nroots) continue;
-        const F2 X_ = add2(gx, rt == 0 ? hy : neg(hy));
-        const F2 Y_ = add2(gy, rt == 0 ? neg(hx) : hx);
-        const double Px = to_f64(X_.hi) + to_f64(X_.lo);
-        const double Py = to_f64(Y_.hi) + to_f64(Y_.lo);
-        o.px[rt] = Px;
-        o.py[rt] = Py;
-        const float pf[3] = {X_.hi, Y_.hi, zf};
-        const bool n1 = pf[0] * p1[0] + pf[1] * p1[1] + pf[2] * p1[2] >= 0.0f;
-        const bool n2 = pf[0] * p2[0] + pf[1] * p2[1] + pf[2] * p2[2] >= 0.0f;
-        const double l1 = n1 ? 1.0 : -1.0, l2 = n2 ? 1.0 : -1.0;
-        const float d1[3] = {f32_scaled(wide::fma64(-l1, x1[0], Px), 0),
-                             f32_scaled(wide::fma64(-l1, x1[1], Py), 0),
-                             f32_scaled(wide::fma64(-l1, x1[2], z0), 0)};
-        const float d2[3] = {f32_scaled(wide::fma64(-l2, x2[0], Px), 0),
-                             f32_scaled(wide::fma64(-l2, x2[1], Py), 0),
-                             f32_scaled(wide::fma64(-l2, x2[2], z0), 0)};
-        const float t1 = wide::fma32(d1[0], m1[0], wide::fma32(d1[1], m1[1], d1[2] * m1[2]));
-        const float t2 = wide::fma32(d2[0], m2[0], wide::fma32(d2[1], m2[1], d2[2] * m2[2]));
-        if (t1 >= 0.0f && t2 >= 0.0f) {
-            o.hit[rt] = true;
+    for (int r = 0; r < 2; ++r) {
+        o.hit[r] = false;
+        if (r >= nroots) continue;
+        const F2 X = add2(gx, r == 0 ? hy : neg(hy));
+        const F2 Y = add2(gy, r == 0 ? neg(hx) : hx);
+        const double Px = to_f64(X.hi) + to_f64(X.lo);
+        const double Py = to_f64(Y.hi) + to_f64(Y.lo);
+        o.px[r] = Px;
+        o.py[r] = Py;
+        if (onarc_test(x1, x2, z0, q, Px, Py)) {
+            o.hit[r] = true;
             ++o.count;
         }
     }
@@ -451,7 +448,7 @@ EFT_HD void intersect_pair(const double (&x1)[3], const double (&x2)[3], double 
     else if (Mode == kWideInt)
         pair_wide(x1, x2, z0, o);
     else
-        pair_ff2(x1, x2, z0, o);
+        pair_ff32(x1, x2, z0, o);
 }
 
 }  // namespace sphx

@@ -168,8 +168,20 @@ sphx_status sphx::ensure_zonal_scratch(sphx_context *ctx, int64_t bands) {
 
 namespace {
 
-sphx_status ensure_scratch(sphx_context *ctx, int64_t E) {
+// The fused scheme needs only the chunk counter; the others the per-edge
+// ranges, their prefix sum and the look-back ring as well.
+sphx_status ensure_scratch(sphx_context *ctx, int64_t E, bool full = true) {
     RaggedScratch &s = ctx->scratch;
+    if (!full) {
+        if (s.counters) return SPHX_OK;
+        if (fault_is("alloc")) return SPHX_ERR_NOMEM;
+        if (cudaMalloc(&s.counters, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            s.counters = nullptr;
+            return SPHX_ERR_NOMEM;
+        }
+        return SPHX_OK;
+    }
     if (s.E >= E && s.ring) return SPHX_OK;
     // growing: nothing may still use the old buffers
     SPHX_CUDA(cudaDeviceSynchronize());
@@ -288,7 +300,7 @@ sphx_status check_ragged_args(const RaggedCall &c) {
 
 RaggedShape effective_shape(const sphx_context *ctx) {
     RaggedShape sh = ctx->shape;
-    if (sh.compaction == SPHX_COMPACT_AUTO) sh.compaction = SPHX_COMPACT_ATOMIC;
+    if (sh.compaction == SPHX_COMPACT_AUTO) sh.compaction = SPHX_COMPACT_FUSED;
     return sh;
 }
 
@@ -298,7 +310,7 @@ sphx_status run_ragged(sphx_context *ctx, const RaggedCall &c, const RaggedShape
         SPHX_CUDA(cudaMemsetAsync(c.out_total, 0, sizeof(int64_t), s));
         return SPHX_OK;
     }
-    sphx_status st = ensure_scratch(ctx, c.E);
+    sphx_status st = ensure_scratch(ctx, c.E, sh.compaction != SPHX_COMPACT_FUSED);
     if (st != SPHX_OK) return st;
     if (!sh.use_graph) {
         SPHX_CUDA(enqueue_ragged(ctx, c, sh, s));
@@ -628,9 +640,10 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
     if (E == 0) return SPHX_OK;
     if ((st = ensure_scratch(ctx, E)) != SPHX_OK) return st;
     const int requested = ctx->shape.compaction;
+    // AUTO: the unordered schemes (the ordered one only when asked for)
     std::vector<int> comps;
     if (requested == SPHX_COMPACT_AUTO)
-        comps = {SPHX_COMPACT_ATOMIC, SPHX_COMPACT_ORDERED, SPHX_COMPACT_FUSED};
+        comps = {SPHX_COMPACT_FUSED, SPHX_COMPACT_ATOMIC};
     else
         comps = {requested};
     cudaEvent_t e0, e1;
@@ -640,7 +653,7 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
     RaggedShape best_sh = effective_shape(ctx);
     for (int comp : comps)
         for (int threads : {128, 256})
-            for (int bps : {2, 4, 8})
+            for (int bps : {4, 8})
                 for (int K : {1, 2, 4}) {
                     if (threads * bps > 2048) continue;
                     // the fused kernel evaluates one queued pair per thread

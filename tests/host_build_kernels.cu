@@ -1,5 +1,5 @@
 // Host builds of the kernels' per-pair and per-cell routines, exported for
-// tests/test_host_builds.py: pair_wide, pair_ff2, pair_accux and pair_direct
+// tests/test_host_builds.py: pair_wide, pair_ff32, pair_accux and pair_direct
 // (paper_2510_09892_gb300/csrc/intersect.cuh), arcs_wide (arcs.cuh), the
 // adaptive filter (adaptive.cuh), the band-area routines (areas.cuh) and the
 // height ranges and latitude searches (ranges.cuh) are __host__ __device__.
@@ -64,14 +64,14 @@ extern "C" void h_pair_accux_printed(const double *A, const double *B, const dou
     run_fp64<2>(A, B, Z, n, pts, cnt);
 }
 
-extern "C" void h_pair_ff2(const double *A, const double *B, const double *Z, long long n,
+extern "C" void h_pair_ff32(const double *A, const double *B, const double *Z, long long n,
                            double *pts, int *cnt) {
     const double nan = __builtin_nan("");
     for (long long i = 0; i < n; ++i) {
         const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
         const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
         sphx::PairOut o;
-        sphx::pair_ff2(x1, x2, Z[i], o);
+        sphx::pair_ff32(x1, x2, Z[i], o);
         for (int r = 0; r < 2; ++r) {
             pts[6 * i + 3 * r + 0] = o.hit[r] ? o.px[r] : nan;
             pts[6 * i + 3 * r + 1] = o.hit[r] ? o.py[r] : nan;

@@ -52,22 +52,11 @@ def norm_error(pts, ref, z0):
         return np.sqrt(d[..., 0] ** 2 + d[..., 1] ** 2) / (U * rho)
 
 
-# float-float's stated bound (s^2 carries about 46 bits, so its absolute error
-# near 2^-46 |n|^2 is amplified by 1 / (2 s) near tangency and near the poles):
-#   |P~ - P| <= 2^-44 sqrt(1 - z0^2) + 2^-45 |n|^2 / (|n_xy| s)
-FF_RHO, FF_COND = 2.0 ** -44, 2.0 ** -45
-
-
-def ff_bound(A, B, z):
-    """Stated float-float bound in units of u sqrt(1 - z0^2) (the norm_error unit)."""
-    n = np.cross(A, B)
-    nxy = np.hypot(n[:, 0], n[:, 1])
-    S3 = (n ** 2).sum(1)
-    s = np.sqrt(np.maximum(nxy ** 2 - S3 * z * z, 0))
-    rho = np.sqrt(np.maximum(0.0, (1 - z) * (1 + z)))
-    with np.errstate(divide="ignore"):
-        b = FF_RHO * rho + FF_COND * S3 / (nxy * s)
-    return b / (U * np.maximum(rho, 1e-300))
+# float-float's stated bound: the cancelling steps (n, |n_xy|^2, s^2) are
+# exact or 128-bit on integer limbs, the rest runs on FP32 pairs (2^-48), and
+# |P~ - P| <= 2^-44 sqrt(1 - z0^2) on every arc; in the norm_error unit
+# (u sqrt(1 - z0^2)) that is 2^-44 / 2^-53 = 512
+FF_BOUND = 2.0 ** -44 / U
 
 
 # Every exact comparison skips the arcs the oracle flags as near a boundary;
