@@ -55,16 +55,16 @@ typedef enum {
        SumOfSquaresC for arcs much shorter than 1e-8 rad or nearly antipodal).
        Error <= 4 ulp per component of the correctly rounded exact point. */
     SPHX_MODE_EFT_FP64 = 1,
-    /* float-float (pairs of FP32 with TwoSum / FMA TwoProd) for endpoints of
-       unit norm: d = x2 -+ x1 in FP64 (the cancelling part of the cross
-       product of nearly coincident or antipodal endpoints), n = x1 x d,
-       |n_xy|^2, |n|^2, s^2, the square root, 1 / |n_xy|^2 and the point in
-       float-float on the FP32 pipe; the on-arc test on FP64 offsets from the
-       endpoints. s^2 carries about 46 bits, so the error grows near tangency
-       and near the poles: |P~ - P| <= 2^-44 sqrt(1 - z0^2)
-       + 2^-45 |n|^2 / (|n_xy| s); hit counts can differ from the exact ones
-       where s^2 is below that resolution. Other endpoints are evaluated as in
-       SPHX_MODE_WIDE_INT. */
+    /* Float-float tail on an exact core (the paper has no such variant; its
+       Sec. 9 names reduced precision as future work): the steps whose
+       cancellation the error analysis of Sec. 4 and 6.1 is about -- the
+       cross product of nearly coincident or antipodal endpoints (exact),
+       |n_xy|^2, |n|^2 and s^2 (128-bit) -- run on 32-bit integer limbs as in
+       SPHX_MODE_WIDE_INT; the square root, 1 / |n_xy|^2 and the point
+       Eq. 2.2 in float-float (pairs of FP32, TwoSum / FMA TwoProd) on the
+       FP32 pipe; the on-arc test as in SPHX_MODE_WIDE_INT. Error
+       |P~ - P| <= 2^-44 sqrt(1 - z0^2) for every arc (near tangency and the
+       poles included), hit counts those of the exact core. */
     SPHX_MODE_EFT_FF32 = 2,
     /* Algorithm 8 exactly as printed (no renormalisation after AccuDOP), for
        comparison; loses accuracy on very short and near-antipodal arcs. */
@@ -392,12 +392,38 @@ sphx_status sphx_get_tuning(sphx_context *ctx, sphx_tuning *tuning);
    keeps the fastest for this context. Synchronises `stream`. If ms_out is not
    NULL (host), it receives the best time in milliseconds. The trial runs
    write out and *out_total; any status they raise (such as a capacity
-   overflow) is cleared before returning. */
+   overflow) is cleared before returning.
+   The result is also kept in the process-wide tuning cache under (device
+   name, mode, the context's requested compaction, floor(log2) of E, of L / M
+   and of M). When the cache already holds that key (found by any context of
+   the process, or read from the file SPHX_TUNE_CACHE names), its shape is
+   applied to ctx without any trial run and ms_out receives the time stored
+   with it. With SPHX_TUNE_CACHE set, every new entry is written to that file
+   (JSON, one entry per line). */
 sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const double *B,
                                  const int64_t *edge_offsets, int32_t M, int64_t E,
                                  const double *lat_z, const int64_t *lat_offsets, int64_t L,
                                  sphx_mode mode, sphx_hit *out, int64_t out_cap,
                                  int64_t *out_total, sphx_stream stream, double *ms_out);
+
+/* Autotune the dense call's grid for `mode`: 1, 2, 4 or 8 waves of resident
+   blocks striding over the tiles of 128 arcs, each timed with CUDA events on
+   the given arrays (arguments as sphx_intersect_gca_constlat, which the
+   trials call and whose outputs they overwrite). The fastest applies to every
+   later dense call of `mode` in the process (the dense call has no context)
+   and goes into the tuning cache under (device name, mode, floor(log2 n)); a
+   cached entry is applied without trial runs. Synchronises `stream`. ms_out
+   (host, may be NULL) receives the best time in milliseconds. */
+sphx_status sphx_autotune_dense(const double *A, const double *B, const double *z0, int64_t n,
+                                double *out_pts, int32_t *out_count, sphx_mode mode,
+                                sphx_stream stream, double *ms_out);
+
+/* Entries the autotuners took from the tuning cache (hits) and found by
+   trial runs (sweeps) since the process started or the last clear. */
+sphx_status sphx_tuning_cache_stats(int64_t *hits, int64_t *sweeps);
+/* Drop the process-wide tuning cache (a file named by SPHX_TUNE_CACHE is read
+   again on next use) and reset the dense grids to one wave. */
+sphx_status sphx_tuning_cache_clear(void);
 
 /* Peak probe of the current device, written to *rate (host); synchronises
    the device. pipe = 0: FP32 FMA, 1: FP64 FMA, in floating-point operations

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -37,7 +38,7 @@ struct RaggedShape {  // defaults: what the autotuner picks on both GB300 worklo
     int threads = 128;
     int blocks_per_sm = 8;
     int pairs_per_lane = 1;
-    int compaction = SPHX_COMPACT_FUSED;
+    int compaction = SPHX_COMPACT_AUTO;  // FUSED until autotuned
     int use_graph = 1;
     bool operator<(const RaggedShape &o) const {
         return std::tie(threads, blocks_per_sm, pairs_per_lane, compaction, use_graph) <
@@ -105,6 +106,21 @@ cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, 
 // fused.cu
 cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
                          cudaStream_t s);
+
+// Process-wide tuning cache (runtime.cu): launch shapes found by the
+// autotuners, keyed by device name, call, mode and a size class, shared by
+// every context of the process and, when SPHX_TUNE_CACHE names a file, kept
+// there as JSON across processes.
+struct TuneEntry {
+    int threads = 0, blocks_per_sm = 0, pairs_per_lane = 0, compaction = 0, waves = 0;
+    double ms = 0.0;
+};
+bool tune_lookup(const std::string &key, TuneEntry &e);
+void tune_store(const std::string &key, const TuneEntry &e);
+std::string tune_device_name();  // of the current device
+// grid of the dense kernels: waves x one wave of resident blocks (default 1)
+int dense_waves(int mode);
+void set_dense_waves(int mode, int waves);
 
 // device staging of the host-buffer dense call: kHostSlots chunks in flight,
 // one stream each (copy in, kernel, copy out stay in order on a slot's

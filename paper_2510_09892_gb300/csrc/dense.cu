@@ -64,3 +64,58 @@ extern "C" sphx_status sphx_accux_intermediates(const double *A, const double *B
     }
     return SPHX_OK;
 }
+
+extern "C" sphx_status sphx_autotune_dense(const double *A, const double *B, const double *z0,
+                                          int64_t n, double *out_pts, int32_t *out_count,
+                                          sphx_mode mode, sphx_stream stream, double *ms_out) {
+    if (n <= 0 || (int)mode < 0 || (int)mode > 5) return SPHX_ERR_INVALID_ARG;
+    char keybuf[256];
+    std::snprintf(keybuf, sizeof keybuf, "%s|dense|mode=%d|n=2^%d", tune_device_name().c_str(),
+                  (int)mode, 63 - __builtin_clzll((unsigned long long)n));
+    const std::string key(keybuf);
+    TuneEntry hit;
+    if (tune_lookup(key, hit)) {
+        set_dense_waves((int)mode, hit.waves);
+        if (ms_out) *ms_out = hit.ms;
+        return SPHX_OK;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    SPHX_CUDA(cudaEventCreate(&e0));
+    SPHX_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_w = 1;
+    for (int w : {1, 2, 4, 8}) {
+        set_dense_waves((int)mode, w);
+        sphx_status st = sphx_intersect_gca_constlat(A, B, z0, n, out_pts, out_count, mode, stream);
+        if (st != SPHX_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            set_dense_waves((int)mode, 1);
+            return st;
+        }
+        float tot = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            SPHX_CUDA(cudaEventRecord(e0, s));
+            sphx_intersect_gca_constlat(A, B, z0, n, out_pts, out_count, mode, stream);
+            SPHX_CUDA(cudaEventRecord(e1, s));
+            SPHX_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (tot / 3 < best) {
+            best = tot / 3;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_dense_waves((int)mode, best_w);
+    if (ms_out) *ms_out = best;
+    TuneEntry te;
+    te.waves = best_w;
+    te.ms = best;
+    tune_store(key, te);
+    return SPHX_OK;
+}

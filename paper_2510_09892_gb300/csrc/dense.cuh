@@ -164,9 +164,10 @@ static void launch_dense(const double *A, const double *B, const double *Z, int6
     static const int sms = sm_count_of_current();
     static const int per_sm = resident_blocks<Mode>();
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    // exactly one wave of resident blocks: a second, partial wave would leave
-    // most SMs idle while it finishes
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+    // one wave of resident blocks striding over the tiles (a second, partial
+    // wave would leave most SMs idle while it finishes), or the multiple of
+    // it that sphx_autotune_dense found fastest
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm * dense_waves(Mode));
     dense_kernel<Mode><<<(unsigned)grid, kTile, 0, s>>>(A, B, Z, n, P, C, fallback,
                                                         0.975 * gate_ulps);
 }

@@ -1,7 +1,10 @@
 // Host runtime of the C ABI: contexts, the device status word, scratch of the
 // ragged call, its CUDA-graph cache and autotuner, and the FMA peak probe.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -18,9 +21,121 @@ void set_cuda_error(cudaError_t e) {
 
 }  // namespace sphx
 
+// ---- process-wide tuning cache -------------------------------------------------
+namespace sphx {
+namespace tunecache {
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune;
+std::string g_tune_file;  // the file g_tune was last loaded from ("" = none)
+bool g_tune_file_read = false;
+long long g_tune_hits = 0, g_tune_sweeps = 0;
+std::atomic<int> g_dense_waves[8] = {{1}, {1}, {1}, {1}, {1}, {1}, {1}, {1}};
+
+std::string tune_file_path() {
+    const char *p = std::getenv("SPHX_TUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+// one entry per line: "key": {"threads": t, "blocks_per_sm": b, "pairs_per_lane": k,
+// "compaction": c, "waves": w, "ms": m}; lines that do not parse are skipped
+void tune_read_locked() {
+    const std::string path = tune_file_path();
+    if (g_tune_file_read && path == g_tune_file) return;
+    g_tune_file_read = true;
+    g_tune_file = path;
+    if (path.empty()) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t q0 = line.find('"');
+        const size_t q1 = q0 == std::string::npos ? q0 : line.find('"', q0 + 1);
+        const size_t br = q1 == std::string::npos ? q1 : line.find('{', q1);
+        if (br == std::string::npos) continue;
+        TuneEntry e;
+        if (std::sscanf(line.c_str() + br,
+                        "{\"threads\": %d, \"blocks_per_sm\": %d, \"pairs_per_lane\": %d, "
+                        "\"compaction\": %d, \"waves\": %d, \"ms\": %lf}",
+                        &e.threads, &e.blocks_per_sm, &e.pairs_per_lane, &e.compaction, &e.waves,
+                        &e.ms) == 6)
+            g_tune[line.substr(q0 + 1, q1 - q0 - 1)] = e;
+    }
+}
+
+void tune_write_locked() {
+    if (g_tune_file.empty()) return;
+    const std::string tmp = g_tune_file + ".tmp";
+    {
+        std::ofstream f(tmp, std::ios::trunc);
+        if (!f) return;
+        f << "{\n";
+        size_t i = 0;
+        for (const auto &kv : g_tune) {
+            const TuneEntry &e = kv.second;
+            char buf[256];
+            std::snprintf(buf, sizeof buf,
+                          "{\"threads\": %d, \"blocks_per_sm\": %d, \"pairs_per_lane\": %d, "
+                          "\"compaction\": %d, \"waves\": %d, \"ms\": %.6f}",
+                          e.threads, e.blocks_per_sm, e.pairs_per_lane, e.compaction, e.waves,
+                          e.ms);
+            f << "  \"" << kv.first << "\": " << buf << (++i < g_tune.size() ? ",\n" : "\n");
+        }
+        f << "}\n";
+    }
+    std::rename(tmp.c_str(), g_tune_file.c_str());
+}
+}  // namespace tunecache
+using namespace tunecache;
+
+bool tune_lookup(const std::string &key, TuneEntry &e) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_read_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    e = it->second;
+    ++g_tune_hits;
+    return true;
+}
+
+void tune_store(const std::string &key, const TuneEntry &e) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tune_read_locked();
+    g_tune[key] = e;
+    ++g_tune_sweeps;
+    tune_write_locked();
+}
+
+std::string tune_device_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown device";
+    }
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || ch == '\n') ch = '_';
+    return name;
+}
+
+int dense_waves(int mode) { return mode >= 0 && mode < 8 ? g_dense_waves[mode].load() : 1; }
+void set_dense_waves(int mode, int waves) {
+    if (mode >= 0 && mode < 8) g_dense_waves[mode].store(waves < 1 ? 1 : waves);
+}
+}  // namespace sphx
+
 using namespace sphx;
 
 namespace {
+
+// floor(log2(v)) for v >= 1 (0 for v < 1): the size classes of the cache keys
+int log2_class(int64_t v) {
+    int c = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++c;
+    }
+    return c;
+}
 
 constexpr int64_t kMaxRingSlots = int64_t(1) << 21;
 
@@ -638,8 +753,28 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
     std::lock_guard<std::mutex> g(ctx->mu);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (E == 0) return SPHX_OK;
-    if ((st = ensure_scratch(ctx, E)) != SPHX_OK) return st;
     const int requested = ctx->shape.compaction;
+    // a shape this process (or the cache file) already found for this device,
+    // mode, requested scheme and size class is taken without a sweep
+    char keybuf[256];
+    std::snprintf(keybuf, sizeof keybuf, "%s|ragged|mode=%d|compaction=%d|E=2^%d|L/M=2^%d|M=2^%d",
+                  tune_device_name().c_str(), (int)mode, requested, log2_class(E),
+                  log2_class(L / (M > 0 ? M : 1)), log2_class(M));
+    const std::string key(keybuf);
+    TuneEntry hit;
+    if (tune_lookup(key, hit)) {
+        RaggedShape sh;
+        sh.threads = hit.threads;
+        sh.blocks_per_sm = hit.blocks_per_sm;
+        sh.pairs_per_lane = hit.pairs_per_lane;
+        sh.compaction = hit.compaction;
+        sh.use_graph = 1;
+        ctx->shape = sh;
+        ctx->tuned = true;
+        if (ms_out) *ms_out = hit.ms;
+        return SPHX_OK;
+    }
+    if ((st = ensure_scratch(ctx, E)) != SPHX_OK) return st;
     // AUTO: the unordered schemes (the ordered one only when asked for)
     std::vector<int> comps;
     if (requested == SPHX_COMPACT_AUTO)
@@ -692,6 +827,31 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
     ctx->shape = best_sh;
     ctx->tuned = true;
     if (ms_out) *ms_out = best;
+    TuneEntry te;
+    te.threads = best_sh.threads;
+    te.blocks_per_sm = best_sh.blocks_per_sm;
+    te.pairs_per_lane = best_sh.pairs_per_lane;
+    te.compaction = best_sh.compaction;
+    te.waves = 1;
+    te.ms = best;
+    tune_store(key, te);
+    return SPHX_OK;
+}
+
+sphx_status sphx_tuning_cache_stats(int64_t *hits, int64_t *sweeps) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    if (hits) *hits = g_tune_hits;
+    if (sweeps) *sweeps = g_tune_sweeps;
+    return SPHX_OK;
+}
+
+sphx_status sphx_tuning_cache_clear(void) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune.clear();
+    g_tune_file_read = false;  // the file (if any) is read again on next use
+    g_tune_file.clear();
+    g_tune_hits = g_tune_sweeps = 0;
+    for (auto &w : g_dense_waves) w.store(1);
     return SPHX_OK;
 }
 

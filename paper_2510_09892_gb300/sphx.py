@@ -74,6 +74,11 @@ _SIGS = {
     "sphx_band_areas": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp,
                                        _vp, ctypes.c_int, _vp, _i64, _vp]),
     "sphx_zonal_sums": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "sphx_autotune_dense": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, ctypes.c_int, _vp,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "sphx_tuning_cache_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_int64)]),
+    "sphx_tuning_cache_clear": (ctypes.c_int, []),
     "sphx_sync_status": (ctypes.c_int, [_vp, _vp]),
     "sphx_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
     "sphx_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(Tuning)]),
@@ -370,6 +375,34 @@ def sphx_autotune_ragged(ctx: Context, A, B, edge_offsets, lat_z, lat_offsets, o
                                     _ptr(out_total), _stream(stream), ctypes.byref(ms))
     _check(st, "sphx_autotune_ragged")
     return ms.value
+
+
+def sphx_autotune_dense(A, B, z0, out_pts, out_count, mode="wide", stream=None) -> float:
+    """Pick the dense call's grid for `mode` on these arrays (or take it from
+    the tuning cache); returns the best time in ms. Overwrites the outputs."""
+    n = int(z0.shape[0])
+    _dev_tensor(A, torch.float64, "A", (n, 3))
+    _dev_tensor(B, torch.float64, "B", (n, 3))
+    _dev_tensor(z0, torch.float64, "z0", (n,))
+    _dev_tensor(out_pts, torch.float64, "out_pts", (n, 2, 3))
+    _dev_tensor(out_count, torch.int32, "out_count", (n,))
+    ms = ctypes.c_double(0.0)
+    st = lib().sphx_autotune_dense(_ptr(A), _ptr(B), _ptr(z0), n, _ptr(out_pts), _ptr(out_count),
+                                   _mode(mode), _stream(stream), ctypes.byref(ms))
+    _check(st, "sphx_autotune_dense")
+    return ms.value
+
+
+def tuning_cache_stats() -> tuple[int, int]:
+    """(hits, sweeps) of the process-wide tuning cache."""
+    h, w = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().sphx_tuning_cache_stats(ctypes.byref(h), ctypes.byref(w)),
+           "sphx_tuning_cache_stats")
+    return h.value, w.value
+
+
+def tuning_cache_clear():
+    _check(lib().sphx_tuning_cache_clear(), "sphx_tuning_cache_clear")
 
 
 # ------------------------------------------------------------- band areas --

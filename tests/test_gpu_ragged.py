@@ -389,3 +389,76 @@ def test_injected_scratch_allocation_failure(monkeypatch):
         key, x, y = all_pairs_reference(batch)
         got, gx, gy = sorted_records(recs)
         assert st == sphx.OK and np.array_equal(got, key) and P.same_bits(gx, x)
+
+
+def test_tuning_cache_reused_by_a_second_context():
+    """The autotuners' results are kept per (device, call, mode, size class):
+    a second context autotuning the same batch takes the shape from the cache
+    without a sweep, and so does the dense autotuner on a second call."""
+    sphx.tuning_cache_clear()
+    batch = small_batch(seed=25)
+    d = to_dev(batch)
+    out = torch.empty(4 * 200_000, dtype=torch.int64, device=DEV)
+    total = torch.empty(1, dtype=torch.int64, device=DEV)
+    with sphx.Context(0) as c1:
+        ms1 = sphx.sphx_autotune_ragged(c1, d["A"], d["B"], d["edge_offsets"], d["lat_z"],
+                                        d["lat_offsets"], out, total, "wide")
+        t1 = c1.get_tuning()
+    assert sphx.tuning_cache_stats() == (0, 1)
+    with sphx.Context(0) as c2:
+        ms2 = sphx.sphx_autotune_ragged(c2, d["A"], d["B"], d["edge_offsets"], d["lat_z"],
+                                        d["lat_offsets"], out, total, "wide")
+        assert c2.get_tuning() == t1 and ms2 == ms1
+        st, n, recs = run_ragged(c2, d, "wide")
+        assert st == sphx.OK and n > 0
+    assert sphx.tuning_cache_stats() == (1, 1)
+    A, B, z = W.uniform_arcs(300_000, seed=26)
+    tA, tB, tz = (torch.from_numpy(v).to(DEV) for v in (A, B, z))
+    pts = torch.empty((len(z), 2, 3), dtype=torch.float64, device=DEV)
+    cnt = torch.empty(len(z), dtype=torch.int32, device=DEV)
+    sphx.sphx_autotune_dense(tA, tB, tz, pts, cnt, "wide")
+    sphx.sphx_autotune_dense(tA, tB, tz, pts, cnt, "wide")
+    assert sphx.tuning_cache_stats() == (2, 2)
+    # the dense call with the tuned grid gives the same results as one wave
+    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "wide")
+    p1, c1_ = pts.cpu().numpy(), cnt.cpu().numpy()
+    sphx.tuning_cache_clear()
+    sphx.sphx_intersect_gca_constlat(tA, tB, tz, pts, cnt, "wide")
+    assert np.array_equal(c1_, cnt.cpu().numpy()) and P.same_bits(p1, pts.cpu().numpy())
+
+
+_CACHE_CHILD = r"""
+import json, sys, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2510_09892_gb300 import sphx, workloads as W
+b = W.ragged_meshes(6, 40, 600, seed=27, lat_min=180, lat_max=500)
+dev = torch.device("cuda:0")
+d = {k: torch.from_numpy(v).to(dev) for k, v in b.items()}
+out = torch.empty(4 * 200000, dtype=torch.int64, device=dev)
+total = torch.empty(1, dtype=torch.int64, device=dev)
+with sphx.Context(0) as c:
+    ms = sphx.sphx_autotune_ragged(c, d["A"], d["B"], d["edge_offsets"], d["lat_z"],
+                                   d["lat_offsets"], out, total, "eft")
+    print(json.dumps({"stats": sphx.tuning_cache_stats(), "tuning": c.get_tuning(), "ms": ms}))
+"""
+
+
+def test_tuning_cache_persists_across_processes(tmp_path):
+    """With SPHX_TUNE_CACHE naming a file, the first process sweeps and writes
+    the entry; a second process reads it and tunes without a sweep."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SPHX_TUNE_CACHE=str(tmp_path / "tune.json"))
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _CACHE_CHILD, root], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert runs[0]["stats"] == [0, 1] and runs[1]["stats"] == [1, 0]
+    assert runs[0]["tuning"] == runs[1]["tuning"]
+    text = (tmp_path / "tune.json").read_text()
+    assert "|ragged|mode=1|" in text and json.loads(text)
