@@ -34,10 +34,10 @@ void set_cuda_error(cudaError_t e);
     } while (0)
 
 // launch shape of the ragged intersection kernel
-struct RaggedShape {  // defaults: what the autotuner picks on both GB300 workloads
-    int threads = 128;
-    int blocks_per_sm = 8;
-    int pairs_per_lane = 1;
+struct RaggedShape {  // defaults: the fastest fused shape on both GB300 workloads
+    int threads = 256;
+    int blocks_per_sm = 4;
+    int pairs_per_lane = 2;  // for the fused kernel: edges per thread and chunk
     int compaction = SPHX_COMPACT_AUTO;  // FUSED until autotuned
     int use_graph = 1;
     bool operator<(const RaggedShape &o) const {

@@ -3,15 +3,16 @@
 // a1, a11, a12 and a2-a10 of the hot path) without the intermediate ranges,
 // prefix sum and their passes over HBM.
 //
-// Each block claims chunks of NT consecutive edges from a global ticket
-// counter (dynamic load balance; edges with many candidates and edges with
-// none cost what they cost). For a chunk:
+// Each block claims chunks of NT x EPT consecutive edges (EPT = 1 or 2 edges
+// per thread) from a global ticket counter (dynamic load balance; edges with
+// many candidates and edges with none cost what they cost). For a chunk:
 //
 //  1. the chunk's mesh: when all its edges lie in one mesh whose latitude grid
-//     fits (kStageLats doubles, 23 KB), that grid is staged in shared memory,
-//     once per mesh change, and every latitude search and latitude read below
-//     goes to shared memory; other chunks read the grids in global memory;
-//  2. one thread per edge: the edge's height range (FP32 for unit endpoints,
+//     fits (kStageLats doubles, 23 KB), that grid is staged in shared memory as
+//     order-preserving integer images, once per mesh change, and every
+//     latitude search and latitude read below goes to shared memory; other
+//     chunks read the grids in global memory;
+//  2. per edge (EPT per thread): the edge's height range (FP32 for unit endpoints,
 //     FP64 otherwise, widened) and two searches into its mesh's sorted
 //     latitudes give the candidate indices [lo, hi) (or the caller's ranges);
 //  3. a block scan of the counts hi - lo numbers the chunk's (edge, latitude)
@@ -34,6 +35,46 @@
 namespace sphx {
 
 constexpr int kStageLats = 2944;  // latitudes of one mesh staged in shared memory (23 KB)
+
+// Searches in a staged grid, which holds the order-preserving integer images
+// (ord64) of the latitudes: the same results as lower_bound_ord and
+// upper_bound_ord_from on the doubles, without the per-probe conversion and
+// with 32-bit indices.
+__device__ __forceinline__ int lower_bound_s(const long long *a, int n, long long key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] >= key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int upper_bound_from_s(const long long *a, int n, int from,
+                                                  long long key) {
+    int lo = from, hi = from, step = 1;
+    while (hi < n && a[hi] <= key) {
+        lo = hi + 1;
+        hi += step;
+        step <<= 1;
+    }
+    if (hi > n) hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > key)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// the double whose ord64 image is o (ord64 is its own inverse on the bits)
+__device__ __forceinline__ double from_ord(long long o) {
+    return __longlong_as_double(o < 0 ? (o ^ 0x7fffffffffffffffLL) : o);
+}
 
 template <int NT>
 __device__ __forceinline__ long long block_inclusive_scan(long long v, long long *ws,
@@ -116,24 +157,26 @@ __device__ __forceinline__ void eval_queue(const FusedArgs &a, int n, const long
 }
 
 // 7 resident blocks of 128 threads per SM (3 of 256): at most 72 (85)
-// registers, which the integer-limb evaluation fits without spills; measured
+// registers (a few bytes of spills in the integer-limb evaluation); measured
 // on GB300 against the unbounded 96: 52.1 -> 49.2 ms on the 512-mesh batch,
-// 0.71 -> 0.65 ms on the cubed sphere
-template <int Mode, int NT>
+// 0.71 -> 0.65 ms on the cubed sphere. Two edges per thread and chunk halve
+// the barriers per edge: 45.7 -> 44.5 ms and 0.626 -> 0.562 ms (256 threads).
+template <int Mode, int NT, int EPT>
 __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs a) {
-    __shared__ double s_lat[kStageLats];
+    constexpr int CH = NT * EPT;              // edges per chunk
+    __shared__ long long s_ord[kStageLats];  // ord64 images of the staged latitudes
     __shared__ long long s_qe[NT];
     __shared__ int s_qk[NT];
     __shared__ double s_qz[NT];
-    __shared__ long long s_incl[NT];
-    __shared__ int s_lo[NT];
+    __shared__ long long s_incl[CH];  // inclusive prefix of pair counts, by slot t EPT + j
+    __shared__ int s_lo[CH];
     __shared__ long long s_ws[32];
     __shared__ long long s_chunk;
     __shared__ int s_m0, s_single;
-    __shared__ int s_staged;  // mesh whose grid s_lat holds (-1: none)
+    __shared__ int s_staged;  // mesh whose grid s_ord holds (-1: none)
 
     const int t = threadIdx.x;
-    const long long nchunks = (a.E + NT - 1) / NT;
+    const long long nchunks = (a.E + CH - 1) / CH;
     if (t == 0) s_staged = -1;
     int qn = 0;  // queue length (the same in every thread)
     while (true) {
@@ -144,10 +187,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs 
                 // the chunk's first mesh; it is the only one if the mesh
                 // extends past the chunk's last edge (offsets are not
                 // validated by the host: clamp what is derived from them)
-                const long long e0 = c * NT;
+                const long long e0 = c * CH;
                 int m = (int)upper_bound_dev<int64_t>(a.edge_offsets, a.M + 1, e0) - 1;
                 m = m < 0 ? 0 : (m >= a.M ? a.M - 1 : m);
-                const long long e_last = min(e0 + NT, (long long)a.E) - 1;
+                const long long e_last = min(e0 + CH, (long long)a.E) - 1;
                 s_m0 = m;
                 s_single = a.edge_offsets[m + 1] > e_last ? 1 : 0;
             }
@@ -155,59 +198,84 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs 
         __syncthreads();
         const long long c = s_chunk;
         if (c >= nchunks) break;
-        const long long e = c * NT + t;
-        const bool valid = e < a.E;
-        int m = s_m0;
         const bool single = s_single != 0;
-        if (!single)
-            while (m < a.M - 1 && a.edge_offsets[m + 1] <= e) ++m;
-        long long ls = a.lat_offsets[m], le = a.lat_offsets[m + 1];
-        ls = ls < 0 ? 0 : (ls > a.L ? a.L : ls);
-        le = le < ls ? ls : (le > a.L ? a.L : le);
-        // stage the mesh's latitudes when the whole chunk is in one mesh
-        const bool staged = single && le - ls <= kStageLats && !a.lo_in;
-        if (staged && s_staged != m) {
+        // the chunk's grid, when all its edges are in one mesh
+        const int m0 = s_m0;
+        long long ls0 = a.lat_offsets[m0], le0 = a.lat_offsets[m0 + 1];
+        ls0 = ls0 < 0 ? 0 : (ls0 > a.L ? a.L : ls0);
+        le0 = le0 < ls0 ? ls0 : (le0 > a.L ? a.L : le0);
+        const bool staged = single && le0 - ls0 <= kStageLats && !a.lo_in;
+        if (staged && s_staged != m0) {
             __syncthreads();  // every thread has read s_staged
-            for (long long i = t; i < le - ls; i += NT) s_lat[i] = a.lat_z[ls + i];
-            if (t == 0) s_staged = m;
+            for (long long i = t; i < le0 - ls0; i += NT) s_ord[i] = ord64(a.lat_z[ls0 + i]);
+            if (t == 0) s_staged = m0;
             __syncthreads();
         }
-        // candidate range of this thread's edge (absolute latitude indices)
-        int32_t lo = (int32_t)ls, hi = (int32_t)ls;
-        if (valid) {
-            if (a.lo_in) {
-                lo = a.lo_in[e];
-                hi = a.hi_in[e];
-            } else {
-                const double x1[3] = {a.A[3 * e], a.A[3 * e + 1], a.A[3 * e + 2]};
-                const double x2[3] = {a.B[3 * e], a.B[3 * e + 1], a.B[3 * e + 2]};
-                double zmin, zmax;
-                const bool finite = finite_bits(x1[0]) && finite_bits(x1[1]) &&
-                                    finite_bits(x1[2]) && finite_bits(x2[0]) &&
-                                    finite_bits(x2[1]) && finite_bits(x2[2]);
-                if (finite &&
-                    (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
-                    const double *lz = staged ? s_lat : a.lat_z + ls;
-                    const int64_t l = lower_bound_ord(lz, le - ls, ord64(zmin));
-                    lo = (int32_t)(ls + l);
-                    hi = (int32_t)(ls + upper_bound_ord_from(lz, le - ls, l, ord64(zmax)));
-                    if (hi < lo) hi = lo;
+        // candidate ranges of this thread's edges c CH + j NT + t (coalesced
+        // across the block for each j), as absolute latitude indices
+        int32_t lo[EPT], hi[EPT];
+        long long own = 0;
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const long long e = c * CH + j * NT + t;
+            int m = m0;
+            if (!single)
+                while (m < a.M - 1 && a.edge_offsets[m + 1] <= e) ++m;
+            long long ls = ls0, le = le0;
+            if (!single) {
+                ls = a.lat_offsets[m];
+                le = a.lat_offsets[m + 1];
+                ls = ls < 0 ? 0 : (ls > a.L ? a.L : ls);
+                le = le < ls ? ls : (le > a.L ? a.L : le);
+            }
+            lo[j] = hi[j] = (int32_t)ls;
+            if (e < a.E) {
+                if (a.lo_in) {
+                    lo[j] = a.lo_in[e];
+                    hi[j] = a.hi_in[e];
+                } else {
+                    const double x1[3] = {a.A[3 * e], a.A[3 * e + 1], a.A[3 * e + 2]};
+                    const double x2[3] = {a.B[3 * e], a.B[3 * e + 1], a.B[3 * e + 2]};
+                    double zmin, zmax;
+                    const bool finite = finite_bits(x1[0]) && finite_bits(x1[1]) &&
+                                        finite_bits(x1[2]) && finite_bits(x2[0]) &&
+                                        finite_bits(x2[1]) && finite_bits(x2[2]);
+                    if (finite &&
+                        (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
+                        if (staged) {
+                            const int n = (int)(le - ls);
+                            const int l = lower_bound_s(s_ord, n, ord64(zmin));
+                            lo[j] = (int32_t)(ls + l);
+                            hi[j] = (int32_t)(ls + upper_bound_from_s(s_ord, n, l, ord64(zmax)));
+                        } else {
+                            const double *lz = a.lat_z + ls;
+                            const int64_t l = lower_bound_ord(lz, le - ls, ord64(zmin));
+                            lo[j] = (int32_t)(ls + l);
+                            hi[j] = (int32_t)(ls + upper_bound_ord_from(lz, le - ls, l,
+                                                                        ord64(zmax)));
+                        }
+                        if (hi[j] < lo[j]) hi[j] = lo[j];
+                    }
                 }
             }
+            own += hi[j] > lo[j] ? (long long)(hi[j] - lo[j]) : 0;
         }
-        const long long cnt = valid && hi > lo ? (long long)(hi - lo) : 0;
         long long total;
-        const long long incl = block_inclusive_scan<NT>(cnt, s_ws, total);
-        s_incl[t] = incl;
-        s_lo[t] = lo;
+        long long run = block_inclusive_scan<NT>(own, s_ws, total) - own;
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            run += hi[j] > lo[j] ? (long long)(hi[j] - lo[j]) : 0;
+            s_incl[t * EPT + j] = run;
+            s_lo[t * EPT + j] = lo[j];
+        }
         __syncthreads();
         // append the chunk's pairs to the queue, evaluating every full queue
         for (long long q = 0; q < total;) {
             const int take = (int)min((long long)(NT - qn), total - q);
             if (t < take) {
                 const long long p = q + t;
-                // the edge holding pair p: first i with s_incl[i] > p
-                int i0 = 0, i1 = NT - 1;
+                // the slot holding pair p: first i with s_incl[i] > p
+                int i0 = 0, i1 = CH - 1;
                 while (i0 < i1) {
                     const int mid = (i0 + i1) >> 1;
                     if (s_incl[mid] > p)
@@ -223,9 +291,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs 
                     atomicOr(a.status, kStatusScratch);
                     kk = -1;
                 } else {
-                    z0 = staged ? s_lat[k - ls] : a.lat_z[k];
+                    z0 = staged ? from_ord(s_ord[k - ls0]) : a.lat_z[k];
                 }
-                s_qe[qn + t] = c * NT + i0;
+                s_qe[qn + t] = c * CH + (i0 % EPT) * NT + i0 / EPT;
                 s_qk[qn + t] = kk;
                 s_qz[qn + t] = z0;
             }
@@ -245,25 +313,35 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs 
 }
 
 template <int Mode>
-static cudaError_t launch_mode(int threads, const FusedArgs &a, unsigned grid, cudaStream_t s) {
+static cudaError_t launch_mode(int threads, int ept, const FusedArgs &a, unsigned grid,
+                               cudaStream_t s) {
     if (threads == 128) {
-        fused_kernel<Mode, 128><<<grid, 128, 0, s>>>(a);
+        if (ept == 1)
+            fused_kernel<Mode, 128, 1><<<grid, 128, 0, s>>>(a);
+        else
+            fused_kernel<Mode, 128, 2><<<grid, 128, 0, s>>>(a);
     } else {
-        fused_kernel<Mode, 256><<<grid, 256, 0, s>>>(a);
+        if (ept == 1)
+            fused_kernel<Mode, 256, 1><<<grid, 256, 0, s>>>(a);
+        else
+            fused_kernel<Mode, 256, 2><<<grid, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
+// threads per block 128 or 256; edges per thread and chunk (the shape's
+// pairs_per_lane field) 1 or 2
 cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
                          cudaStream_t s) {
     const int threads = sh.threads <= 128 ? 128 : 256;
+    const int ept = sh.pairs_per_lane >= 2 ? 2 : 1;
     const unsigned grid = (unsigned)(sm_count * sh.blocks_per_sm);
     switch (mode) {
-        case kDirect: return launch_mode<kDirect>(threads, a, grid, s);
-        case kEftFp64: return launch_mode<kEftFp64>(threads, a, grid, s);
-        case kEftFf32: return launch_mode<kEftFf32>(threads, a, grid, s);
-        case kWideInt: return launch_mode<kWideInt>(threads, a, grid, s);
-        default: return launch_mode<kEftFp64Printed>(threads, a, grid, s);
+        case kDirect: return launch_mode<kDirect>(threads, ept, a, grid, s);
+        case kEftFp64: return launch_mode<kEftFp64>(threads, ept, a, grid, s);
+        case kEftFf32: return launch_mode<kEftFf32>(threads, ept, a, grid, s);
+        case kWideInt: return launch_mode<kWideInt>(threads, ept, a, grid, s);
+        default: return launch_mode<kEftFp64Printed>(threads, ept, a, grid, s);
     }
 }
 

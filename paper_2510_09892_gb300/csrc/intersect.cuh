@@ -221,6 +221,19 @@ SPHX_HD float f32_scaled(double x, int sc) {
                           (uint32_t)((b >> 29) & 0x7fffffu));
 }
 
+// f32_scaled(x, 0) in fewer instructions, bit for bit for every input: a
+// funnel shift brings the double's low 9 exponent bits and top 23 mantissa
+// bits into place, and keeping 8 bits of (exponent - 384) gives the float's
+// exponent field (1023 - 127 = 896 = 512 + 384) over the whole float range
+SPHX_HD float f32_of(double x) {
+    const uint64_t b = wide::bits_of(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t f = wide::funnel_l(lo, hi, 3), sign = hi & 0x80000000u, e2 = hi << 1;
+    const uint32_t v = e2 >= (1151u << 21) ? (sign | (254u << 23) | (f & 0x7fffffu))
+                                           : (((f - (384u << 23)) & 0x7fffffffu) | sign);
+    return e2 >= (897u << 21) ? wide::float_of(v) : 0.0f;
+}
+
 // 0.M 2^(e - emax) of a W<4> as a float
 SPHX_HD float f32_rel(const wide::W<4> &a, int emax) {
     const int fe = a.e - emax + 126;

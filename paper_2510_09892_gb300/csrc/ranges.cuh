@@ -187,8 +187,8 @@ EFT_HD bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
     float p1[3], p2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        p1[i] = f32_scaled(x1[i], 0);
-        p2[i] = f32_scaled(x2[i], 0);
+        p1[i] = f32_of(x1[i]);
+        p2[i] = f32_of(x2[i]);
     }
     const float q1 = p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2];
     const float q2 = p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2];
@@ -205,7 +205,7 @@ EFT_HD bool z_range_fp32(const double (&x1)[3], const double (&x2)[3],
     const double sg = (p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2] >= 0.0f) ? 1.0 : -1.0;
     float d[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = f32_scaled(x2[i] - sg * x1[i], 0);
+    for (int i = 0; i < 3; ++i) d[i] = f32_of(x2[i] - sg * x1[i]);
     const float nx = fmaf(p1[1], d[2], -p1[2] * d[1]);
     const float ny = fmaf(p1[2], d[0], -p1[0] * d[2]);
     const float nz = fmaf(p1[0], d[1], -p1[1] * d[0]);

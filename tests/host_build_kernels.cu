@@ -237,3 +237,13 @@ extern "C" void h_accux_mid(const double *A, const double *B, const double *Z, l
         sphx::pair_accux<true>(x1, x2, Z[i], o, mid + 16 * i);
     }
 }
+
+// the fast FP64 -> FP32 conversion against the general one, on given bit patterns
+extern "C" long long h_f32_of_mismatches(const double *x, long long n) {
+    long long bad = 0;
+    for (long long i = 0; i < n; ++i) {
+        const float a = sphx::f32_of(x[i]), b = sphx::f32_scaled(x[i], 0);
+        if (sphx::wide::fbits_of(a) != sphx::wide::fbits_of(b)) ++bad;
+    }
+    return bad;
+}

@@ -166,16 +166,18 @@ def fused_batches(kind):
             "lat_z": W.latlon_latitudes(181), "lat_offsets": np.array([0, 181], dtype=np.int64)}
 
 
-@pytest.mark.parametrize("threads,bps", [(128, 4), (256, 2)])
+@pytest.mark.parametrize("threads,bps,ept", [(128, 4, 1), (256, 2, 1), (128, 4, 2),
+                                             (256, 3, 2)])
 @pytest.mark.parametrize("kind", ["cubed", "tiny_meshes", "big_grids", "empty_mesh", "one_edge"])
 @pytest.mark.parametrize("mode", ["eft", "direct"])
-def test_fused_kernel_equals_all_pairs_reference(ctx, mode, kind, threads, bps):
+def test_fused_kernel_equals_all_pairs_reference(ctx, mode, kind, threads, bps, ept):
     """The fused ragged kernel (ranges, pair queue and evaluation in one
-    launch): the same records as brute force over every (edge, latitude) pair
-    with the step reference, bit for bit, on every path of the kernel."""
+    launch; 1 or 2 edges per thread and chunk): the same records as brute
+    force over every (edge, latitude) pair with the step reference, bit for
+    bit, on every path of the kernel."""
     batch = fused_batches(kind)
     d = to_dev(batch)
-    ctx.set_tuning(threads_per_block=threads, blocks_per_sm=bps,
+    ctx.set_tuning(threads_per_block=threads, blocks_per_sm=bps, pairs_per_lane=ept,
                    compaction=sphx.COMPACT_FUSED, use_graph=1)
     st, total, recs = run_ragged(ctx, d, mode)
     ctx.reset_tuning()

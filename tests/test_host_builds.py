@@ -202,6 +202,8 @@ def pair_lib():
                                                           ctypes.c_void_p, ctypes.c_void_p,
                                                           ctypes.c_void_p]
     vp, ll = ctypes.c_void_p, ctypes.c_longlong
+    L.h_f32_of_mismatches.argtypes = [vp, ll]
+    L.h_f32_of_mismatches.restype = ll
     L.h_green_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp]
     L.h_green_cells.restype = ctypes.c_uint
     L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
@@ -304,6 +306,23 @@ def test_float_float_on_the_host_within_stated_bound(pair_lib, gen):
     assert np.array_equal(np.isfinite(pts[..., 0]) & ok[:, None], hit)
     err = P.norm_error(pts, pe, z)
     assert np.nanmax(np.where(hit, err, 0)) <= P.FF_BOUND
+
+
+def test_fast_fp32_conversion_equals_general_one(pair_lib):
+    """f32_of (the range code's FP64 -> FP32 conversion) gives the bits of
+    f32_scaled(x, 0) on every exponent (each of the 2048 exponent fields with
+    random mantissas and both signs, zeros, subnormals, infinities, NaN)."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    ex = np.repeat(np.arange(2048, dtype=np.uint64), 64)
+    mant = rng.integers(0, 1 << 52, ex.size, dtype=np.uint64)
+    sign = rng.integers(0, 2, ex.size, dtype=np.uint64)
+    bits = (sign << np.uint64(63)) | (ex << np.uint64(52)) | mant
+    x = np.ascontiguousarray(bits.view(np.float64))
+    assert pair_lib.h_f32_of_mismatches(x.ctypes.data, x.size) == 0
+    edge = np.array([0.0, -0.0, 1.0, -1.0, 2.0 ** -126, 2.0 ** -127, 2.0 ** 127, 2.0 ** 128,
+                     np.inf, -np.inf, np.nan, 5e-324, 1.9999999999999998])
+    assert pair_lib.h_f32_of_mismatches(edge.ctypes.data, edge.size) == 0
 
 
 @pytest.mark.parametrize("form", ["accux", "accux_printed", "direct"])
