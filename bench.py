@@ -334,6 +334,8 @@ def main():
                     help="run only the cubed-sphere regridding leg and print its JSON (for profiling)")
     ap.add_argument("--meshes-only", action="store_true",
                     help="run only the 512-mesh ragged leg and print its JSON (for profiling)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="ragged legs with the library's default launch shape (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -667,8 +669,8 @@ def ragged_leg(sphx, torch, dev, args, head) -> dict:
     with sphx.Context(dev.index or 0) as ctx:
         for mode in (head, "eft", "direct"):
             ctx.reset_tuning()
-            tune_ms = sphx.sphx_autotune_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
-                                                total, mode, stream=cur)
+            tune_ms = None if args.no_autotune else sphx.sphx_autotune_ragged(
+                ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out, total, mode, stream=cur)
             for _ in range(args.warmup):
                 sphx.sphx_intersect_ragged(ctx, d["A"], d["B"], d["eo"], d["lat"], d["lo"], out,
                                            total, mode, stream=cur)
@@ -789,8 +791,8 @@ def meshes_leg(sphx, torch, dev, args, head, pool) -> dict:
     with sphx.Context(dev.index or 0) as ctx:
         for mode in (head, "eft", "direct"):
             ctx.reset_tuning()
-            tune_ms = sphx.sphx_autotune_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
-                                                stream=cur)
+            tune_ms = None if args.no_autotune else sphx.sphx_autotune_ragged(
+                ctx, tA, tB, teo, tlat, tlo, out, total, mode, stream=cur)
             for _ in range(3):
                 sphx.sphx_intersect_ragged(ctx, tA, tB, teo, tlat, tlo, out, total, mode,
                                            stream=cur)

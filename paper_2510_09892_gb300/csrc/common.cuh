@@ -103,6 +103,10 @@ cudaError_t launch_scan(const int32_t *lo, const int32_t *hi, int64_t E, long lo
                         long long *offsets, cudaStream_t s);
 cudaError_t launch_ragged(int mode, const RaggedShape &sh, const RaggedArgs &a, int sm_count,
                           cudaStream_t s);
+// dense.cu: the dense call on page-locked host arrays read in place
+sphx_status dense_host_inplace(const double *A, const double *B, const double *z0, int64_t n,
+                               double *out_pts, int32_t *out_count, sphx_mode mode,
+                               cudaStream_t s);
 // fused.cu
 cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
                          cudaStream_t s);

@@ -36,6 +36,28 @@ extern "C" sphx_status sphx_intersect_gca_constlat(const double *A, const double
 }
 
 namespace sphx {
+sphx_status dense_host_inplace(const double *A, const double *B, const double *z0, int64_t n,
+                               double *out_pts, int32_t *out_count, sphx_mode mode,
+                               cudaStream_t s) {
+    switch (mode) {
+        case SPHX_MODE_DIRECT_FP64: launch_dense_plain<kDirect>(A, B, z0, n, out_pts, out_count, s); break;
+        case SPHX_MODE_EFT_FP64: launch_dense_plain<kEftFp64>(A, B, z0, n, out_pts, out_count, s); break;
+        case SPHX_MODE_EFT_FF32: launch_dense_plain<kEftFf32>(A, B, z0, n, out_pts, out_count, s); break;
+        case SPHX_MODE_EFT_FP64_PRINTED:
+            launch_dense_plain<kEftFp64Printed>(A, B, z0, n, out_pts, out_count, s);
+            break;
+        case SPHX_MODE_WIDE_INT: launch_dense_plain<kWideInt>(A, B, z0, n, out_pts, out_count, s); break;
+        case SPHX_MODE_ADAPTIVE: launch_adaptive(A, B, z0, n, out_pts, out_count, 4.0, nullptr, s); break;
+        default: return SPHX_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return SPHX_ERR_CUDA;
+    }
+    return SPHX_OK;
+}
+
 __global__ void accux_mid_kernel(const double *__restrict__ A, const double *__restrict__ B,
                                  const double *__restrict__ Z, int64_t n, double *__restrict__ mid) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

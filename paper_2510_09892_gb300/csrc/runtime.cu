@@ -641,8 +641,11 @@ sphx_status sphx_intersect_gca_constlat_host(sphx_context *ctx, const double *A,
         HostStaging &h = ctx->host;
         SPHX_CUDA(cudaEventRecord(h.start, us));
         SPHX_CUDA(cudaStreamWaitEvent(h.s[0], h.start, 0));
-        return sphx_intersect_gca_constlat(A, B, z0, n, out_pts, out_count, mode,
-                                           reinterpret_cast<sphx_stream>(h.s[0]));
+        auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+        if (misaligned(A) || misaligned(B) || misaligned(z0) || misaligned(out_pts) ||
+            misaligned(out_count))
+            return SPHX_ERR_INVALID_ARG;
+        return dense_host_inplace(A, B, z0, n, out_pts, out_count, mode, h.s[0]);
     }
     int64_t chunk = (n + kHostSlots - 1) / kHostSlots;
     chunk = std::min<int64_t>(kHostMaxChunk, (chunk + 127) / 128 * 128);
