@@ -64,12 +64,18 @@ FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
 # Thread instructions per arc of dense_kernel<WIDE>, from one ncu capture
 # (smsp__inst_executed.sum x 32 / arcs): a property of the compiled kernel,
 # valid only for the build it was taken on, reported as a secondary figure.
-INST_PER_ARC = {"wide": {"value": 2351, "source": "ncu smsp__inst_executed.sum x 32 / arcs, "
-                         "10^6 stress arcs, profiles/dense_kernel_wide_stress_1e6.md "
-                         "(kernel as of commit 7822872)"}}
+INST_PER_ARC = {"wide": {"value": 2329, "source": "ncu smsp__inst_executed.sum x 32 / arcs, "
+                         "10^7 arcs of the mixed workload, "
+                         "profiles/dense_pf_kernel_wide_mixed_1e7.md (kernel as of commit "
+                         "7a7e4e6)"}}
 # DRAM bytes (read + write) per arc of one launch, from an ncu capture of a
-# launch larger than L2; None where no capture matches the current kernel.
-TRAFFIC_PER_ARC = {"wide": None}
+# launch larger than L2 (scaled to the launch by its arcs); None where no
+# capture matches the current kernel.
+TRAFFIC_PER_ARC = {"wide": {"value": (561160448 + 477118208) / 1e7,
+                            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                      "launch over 10^7 arcs of the mixed workload, scaled by "
+                                      "the arcs, profiles/dense_pf_kernel_wide_mixed_1e7.md "
+                                      "(kernel as of commit 7a7e4e6)"}}
 ISSUE_SLOTS_PER_SM_CLK = 4 * 32  # 4 schedulers, one warp instruction each per clock
 SM_MAX_MHZ = 2070.0
 DTYPES = {"wide": "u32 limbs (128/96-bit mantissas), f64 in/out", "eft": "f64",
@@ -463,7 +469,7 @@ def main():
     tpa = TRAFFIC_PER_ARC.get(head)
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": hbm_peak,
                 "frac": gbs / hbm_peak, "traffic": None if tpa is None else tpa["value"] * n,
-                "kernel": f"dense_kernel<{head}>", "launch_ms": head_kernel_ms,
+                "kernel": f"dense_pf_kernel<{head}>", "launch_ms": head_kernel_ms,
                 "per_unit": f"{BYTES_PER_ARC} B per arc (56 in, 48 points + 4 count out) x "
                             f"{n} arcs per launch",
                 "peak_source": hbm_src}
