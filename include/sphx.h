@@ -116,7 +116,7 @@ typedef struct {
     int32_t threads_per_block; /* 64..1024, multiple of 32 */
     int32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SM count */
     int32_t pairs_per_lane;    /* ATOMIC, ORDERED: candidate pairs a lane takes per claimed
-                                  chunk (1, 2, 4); FUSED: edges per thread per chunk (1, 2) */
+                                  chunk (1, 2, 4); FUSED: edges per thread per chunk (1, 2, 4) */
     int32_t compaction;        /* sphx_compaction */
     int32_t use_graph;         /* 1: capture the ragged launch sequence in a CUDA graph */
 } sphx_tuning;

@@ -3,8 +3,8 @@
 // a1, a11, a12 and a2-a10 of the hot path) without the intermediate ranges,
 // prefix sum and their passes over HBM.
 //
-// Each block claims chunks of NT x EPT consecutive edges (EPT = 1 or 2 edges
-// per thread) from a global ticket counter (dynamic load balance; edges with
+// Each block claims chunks of NT x EPT consecutive edges (EPT = 1, 2 or 4
+// edges per thread) from a global ticket counter (dynamic load balance; edges with
 // many candidates and edges with none cost what they cost). For a chunk:
 //
 //  1. the chunk's mesh: when all its edges lie in one mesh whose latitude grid
@@ -160,7 +160,8 @@ __device__ __forceinline__ void eval_queue(const FusedArgs &a, int n, const long
 // registers (a few bytes of spills in the integer-limb evaluation); measured
 // on GB300 against the unbounded 96: 52.1 -> 49.2 ms on the 512-mesh batch,
 // 0.71 -> 0.65 ms on the cubed sphere. Two edges per thread and chunk halve
-// the barriers per edge: 45.7 -> 44.5 ms and 0.626 -> 0.562 ms (256 threads).
+// the barriers per edge: 45.7 -> 44.5 ms and 0.626 -> 0.562 ms (256 threads);
+// four: 44.7 ms and 0.539 ms.
 template <int Mode, int NT, int EPT>
 __global__ void __launch_bounds__(NT, NT == 128 ? 7 : 3) fused_kernel(FusedArgs a) {
     constexpr int CH = NT * EPT;              // edges per chunk
@@ -318,23 +319,27 @@ static cudaError_t launch_mode(int threads, int ept, const FusedArgs &a, unsigne
     if (threads == 128) {
         if (ept == 1)
             fused_kernel<Mode, 128, 1><<<grid, 128, 0, s>>>(a);
-        else
+        else if (ept == 2)
             fused_kernel<Mode, 128, 2><<<grid, 128, 0, s>>>(a);
+        else
+            fused_kernel<Mode, 128, 4><<<grid, 128, 0, s>>>(a);
     } else {
         if (ept == 1)
             fused_kernel<Mode, 256, 1><<<grid, 256, 0, s>>>(a);
-        else
+        else if (ept == 2)
             fused_kernel<Mode, 256, 2><<<grid, 256, 0, s>>>(a);
+        else
+            fused_kernel<Mode, 256, 4><<<grid, 256, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
 // threads per block 128 or 256; edges per thread and chunk (the shape's
-// pairs_per_lane field) 1 or 2
+// pairs_per_lane field) 1, 2 or 4
 cudaError_t launch_fused(int mode, const RaggedShape &sh, const FusedArgs &a, int sm_count,
                          cudaStream_t s) {
     const int threads = sh.threads <= 128 ? 128 : 256;
-    const int ept = sh.pairs_per_lane >= 2 ? 2 : 1;
+    const int ept = sh.pairs_per_lane >= 4 ? 4 : (sh.pairs_per_lane >= 2 ? 2 : 1);
     const unsigned grid = (unsigned)(sm_count * sh.blocks_per_sm);
     switch (mode) {
         case kDirect: return launch_mode<kDirect>(threads, ept, a, grid, s);

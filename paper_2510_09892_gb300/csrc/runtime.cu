@@ -794,8 +794,6 @@ sphx_status sphx_autotune_ragged(sphx_context *ctx, const double *A, const doubl
             for (int bps : {4, 8})
                 for (int K : {1, 2, 4}) {
                     if (threads * bps > 2048) continue;
-                    // the fused kernel takes 1 or 2 edges per thread and chunk
-                    if (comp == SPHX_COMPACT_FUSED && K == 4) continue;
                     RaggedShape sh;
                     sh.threads = threads;
                     sh.blocks_per_sm = bps;

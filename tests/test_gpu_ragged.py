@@ -167,12 +167,12 @@ def fused_batches(kind):
 
 
 @pytest.mark.parametrize("threads,bps,ept", [(128, 4, 1), (256, 2, 1), (128, 4, 2),
-                                             (256, 3, 2)])
+                                             (256, 3, 2), (128, 8, 4), (256, 4, 4)])
 @pytest.mark.parametrize("kind", ["cubed", "tiny_meshes", "big_grids", "empty_mesh", "one_edge"])
 @pytest.mark.parametrize("mode", ["eft", "direct"])
 def test_fused_kernel_equals_all_pairs_reference(ctx, mode, kind, threads, bps, ept):
     """The fused ragged kernel (ranges, pair queue and evaluation in one
-    launch; 1 or 2 edges per thread and chunk): the same records as brute
+    launch; 1, 2 or 4 edges per thread and chunk): the same records as brute
     force over every (edge, latitude) pair with the step reference, bit for
     bit, on every path of the kernel."""
     batch = fused_batches(kind)
