@@ -52,9 +52,12 @@ __global__ void candidate_kernel(const double *__restrict__ A, const double *__r
         const double x2[3] = {B[3 * e], B[3 * e + 1], B[3 * e + 2]};
         int32_t lo = (int32_t)ls, hi = (int32_t)ls;
         double zmin, zmax;
-        const bool finite = finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) &&
-                            finite_bits(x2[0]) && finite_bits(x2[1]) && finite_bits(x2[2]);
-        if (finite && (z_range_fp32(x1, x2, zmin, zmax) || z_range_fp64(x1, x2, zmin, zmax))) {
+        // the FP32 range fails for every non-finite endpoint (its unit-norm
+        // test does), so only the FP64 one needs the finiteness check
+        if (z_range_fp32(x1, x2, zmin, zmax) ||
+            (finite_bits(x1[0]) && finite_bits(x1[1]) && finite_bits(x1[2]) &&
+             finite_bits(x2[0]) && finite_bits(x2[1]) && finite_bits(x2[2]) &&
+             z_range_fp64(x1, x2, zmin, zmax))) {
             const double *lz = lat_z + ls;
             const int64_t l = lower_bound_ord(lz, le - ls, ord64(zmin));
             lo = (int32_t)(ls + l);

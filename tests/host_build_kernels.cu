@@ -186,15 +186,20 @@ extern "C" void h_pair_cells(const double *nodes, long long n_nodes,
     delete[] off;
 }
 
-// the candidate kernel's height range of each arc (z_range_fp32, else
-// z_range_fp64, as in ragged.cu); ok[i] = 0 where neither gives one
+// the candidate kernels' height range of each arc (z_range_fp32, else
+// z_range_fp64 for finite endpoints, as in ragged.cu and fused.cu); ok[i] = 0
+// where neither gives one. fp32[i] = 1 where the FP32 range alone gives it.
 extern "C" void h_z_ranges(const double *A, const double *B, long long n, double *zmin,
-                           double *zmax, int *ok) {
+                           double *zmax, int *ok, int *fp32) {
     for (long long i = 0; i < n; ++i) {
         const double x1[3] = {A[3 * i], A[3 * i + 1], A[3 * i + 2]};
         const double x2[3] = {B[3 * i], B[3 * i + 1], B[3 * i + 2]};
         double lo = 0.0, hi = 0.0;
-        ok[i] = (sphx::z_range_fp32(x1, x2, lo, hi) || sphx::z_range_fp64(x1, x2, lo, hi)) ? 1 : 0;
+        bool finite = true;
+        for (int k = 0; k < 3; ++k) finite = finite && sphx::finite_bits(x1[k]) && sphx::finite_bits(x2[k]);
+        const bool f32 = sphx::z_range_fp32(x1, x2, lo, hi);
+        fp32[i] = f32 ? 1 : 0;
+        ok[i] = (f32 || (finite && sphx::z_range_fp64(x1, x2, lo, hi))) ? 1 : 0;
         zmin[i] = lo;
         zmax[i] = hi;
     }

@@ -208,7 +208,7 @@ def pair_lib():
     L.h_green_cells.restype = ctypes.c_uint
     L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
     L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
-    L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp]
+    L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp, vp]
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
     L.h_from_fixed.argtypes = [vp, vp, ll, vp]
@@ -476,8 +476,9 @@ def test_candidate_height_ranges_contain_the_arcs(pair_lib, gen):
     n = len(A)
     zmin, zmax = np.empty(n), np.empty(n)
     ok = np.empty(n, dtype=np.int32)
+    f32 = np.empty(n, dtype=np.int32)
     pair_lib.h_z_ranges(A.ctypes.data, B.ctypes.data, n, zmin.ctypes.data, zmax.ctypes.data,
-                        ok.ctypes.data)
+                        ok.ctypes.data, f32.ctypes.data)
     assert ok.all()
     lo = np.empty(n)
     hi = np.empty(n)
@@ -486,6 +487,41 @@ def test_candidate_height_ranges_contain_the_arcs(pair_lib, gen):
         lo[i], hi[i] = min(zs), max(zs)
     assert (zmin <= lo).all() and (zmax >= hi).all()
     assert ((zmax - zmin) - (hi - lo) <= 8 * 2.0 ** -19).all()
+
+
+def test_fp32_height_range_refuses_non_finite_endpoints(pair_lib):
+    """The candidate kernels test finiteness only before the FP64 height range:
+    the FP32 range must give none for an endpoint with an infinite or NaN
+    coordinate (any of the six, either sign, NaN payloads included) or one
+    scaled to the largest doubles, while it gives one for the same arcs with
+    finite unit endpoints."""
+    import numpy as np
+    from paper_2510_09892_gb300 import workloads as W
+    A0, B0, _ = W.uniform_arcs(64, seed=108)
+    bad_values = [np.inf, -np.inf, np.nan, -np.nan,
+                  np.frombuffer(np.uint64(0x7ff0000000000001).tobytes(), np.float64)[0],
+                  np.frombuffer(np.uint64(0xfff8dead00000000).tobytes(), np.float64)[0],
+                  1.7e308, -1.7e308]
+    rows_A, rows_B = [], []
+    for v in bad_values:
+        for k in range(6):
+            A, B = A0.copy(), B0.copy()
+            (A if k < 3 else B)[:, k % 3] = v
+            rows_A.append(A)
+            rows_B.append(B)
+    A = np.ascontiguousarray(np.concatenate(rows_A + [A0]))
+    B = np.ascontiguousarray(np.concatenate(rows_B + [B0]))
+    n = len(A)
+    zmin, zmax = np.empty(n), np.empty(n)
+    ok = np.empty(n, dtype=np.int32)
+    f32 = np.empty(n, dtype=np.int32)
+    pair_lib.h_z_ranges(A.ctypes.data, B.ctypes.data, n, zmin.ctypes.data, zmax.ctypes.data,
+                        ok.ctypes.data, f32.ctypes.data)
+    bad = slice(0, n - len(A0))
+    assert not f32[bad].any()
+    finite = np.isfinite(A).all(1) & np.isfinite(B).all(1)
+    assert not ok[bad][~finite[bad]].any()
+    assert f32[n - len(A0):].all() and ok[n - len(A0):].all()
 
 
 def test_latitude_searches_on_the_host(pair_lib):
