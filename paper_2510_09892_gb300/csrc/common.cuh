@@ -37,7 +37,7 @@ void set_cuda_error(cudaError_t e);
 struct RaggedShape {  // defaults: the fastest fused shape on both GB300 workloads
     int threads = 256;
     int blocks_per_sm = 4;
-    int pairs_per_lane = 2;  // for the fused kernel: edges per thread and chunk
+    int pairs_per_lane = 4;  // for the fused kernel: edges per thread and chunk
     int compaction = SPHX_COMPACT_AUTO;  // FUSED until autotuned
     int use_graph = 1;
     bool operator<(const RaggedShape &o) const {
