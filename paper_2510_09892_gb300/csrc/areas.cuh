@@ -360,7 +360,7 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
                                        fma(v0[1], d1z * d2x - d1x * d2z,
                                            v0[2] * (d1x * d2y - d1y * d2x)));
                 const double t = tri / (1.0 + oa + ab + ob);
-                area += 2.0 * (fabs(t) <= 0.001953125 ? atan_small(t) : atan(t));
+                area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
                 a[0] = b[0];
                 a[1] = b[1];
                 a[2] = b[2];
@@ -368,7 +368,7 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
         }
         if (!ok) return false;
         if (far) return true;
-        areas[off] = area;
+        areas[off] = 2.0 * area;  // the doubling is exact: the same as doubling each term
         return false;
     }
 }
@@ -388,8 +388,9 @@ EFT_HD bool fan_of(const double (*p)[3], int n, double &area) {
         const double tri = fma(o[0], d1y * d2z - d1z * d2y,
                                fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
         const double t = tri / (1.0 + oa + ab + ob);
-        area += 2.0 * (fabs(t) <= 0.001953125 ? atan_small(t) : atan(t));
+        area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
     }
+    area *= 2.0;  // the doubling is exact: the same as doubling each term
     return true;
 }
 
@@ -511,7 +512,10 @@ EFT_HD bool pair_area(const Mesh &m, int64_t f,
     double sliver;
     if (t <= 0.001953125) {
         const double z2 = z * z, t2 = t * t;
-        const double poly = fma(t2, fma(t2, fma(z2, z2, z2 + 1.0) / 7.0, -(1.0 + z2) / 5.0),
+        // the coefficients' divisions by 7 and 5 as products with the
+        // constants' reciprocals (an FP64 division costs several FMAs)
+        const double poly = fma(t2, fma(t2, fma(z2, z2, z2 + 1.0) * (1.0 / 7.0),
+                                        (1.0 + z2) * (-1.0 / 5.0)),
                                 1.0 / 3.0);
         sliver = 2.0 * z * rho2 * (t * t2) * poly;
     } else {
