@@ -346,15 +346,17 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
             unit(u, v0);
             if (ok) ok = node_at(m, s + 1, u);
             unit(u, a);
-            far = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2])) < 0.5;
+            // node 0's dot product with a and the difference a - node 0 carry
+            // over from one triangle to the next (b becomes a)
+            double oa = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2]));
+            double d1x = a[0] - v0[0], d1y = a[1] - v0[1], d1z = a[2] - v0[2];
+            far = oa < 0.5;
             for (int64_t j = s + 2; j < e && ok && !far; ++j) {
                 if (!(ok = node_at(m, j, u))) break;
                 unit(u, b);
                 const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
                 const double ob = fma(v0[0], b[0], fma(v0[1], b[1], v0[2] * b[2]));
-                const double oa = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2]));
                 far = ob < 0.5;
-                const double d1x = a[0] - v0[0], d1y = a[1] - v0[1], d1z = a[2] - v0[2];
                 const double d2x = b[0] - v0[0], d2y = b[1] - v0[1], d2z = b[2] - v0[2];
                 const double tri = fma(v0[0], d1y * d2z - d1z * d2y,
                                        fma(v0[1], d1z * d2x - d1x * d2z,
@@ -364,6 +366,10 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
                 a[0] = b[0];
                 a[1] = b[1];
                 a[2] = b[2];
+                oa = ob;
+                d1x = d2x;
+                d1y = d2y;
+                d1z = d2z;
             }
         }
         if (!ok) return false;
@@ -377,18 +383,27 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
 // is more than 60 degrees from p[0]
 EFT_HD bool fan_of(const double (*p)[3], int n, double &area) {
     area = 0.0;
+    if (n < 3) return true;
+    const double *o = p[0];
+    // p[0]'s dot product with p[i] and the difference p[i] - p[0] carry over
+    // from one triangle to the next
+    double oa = fma(o[0], p[1][0], fma(o[1], p[1][1], o[2] * p[1][2]));
+    double d1x = p[1][0] - o[0], d1y = p[1][1] - o[1], d1z = p[1][2] - o[2];
+    if (oa < 0.5) return false;
     for (int i = 1; i + 1 < n; ++i) {
-        const double *a = p[i], *b = p[i + 1], *o = p[0];
-        const double oa = fma(o[0], a[0], fma(o[1], a[1], o[2] * a[2]));
+        const double *a = p[i], *b = p[i + 1];
         const double ob = fma(o[0], b[0], fma(o[1], b[1], o[2] * b[2]));
         const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
-        if (oa < 0.5 || ob < 0.5) return false;
-        const double d1x = a[0] - o[0], d1y = a[1] - o[1], d1z = a[2] - o[2];
+        if (ob < 0.5) return false;
         const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
         const double tri = fma(o[0], d1y * d2z - d1z * d2y,
                                fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
         const double t = tri / (1.0 + oa + ab + ob);
         area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
+        oa = ob;
+        d1x = d2x;
+        d1y = d2y;
+        d1z = d2z;
     }
     area *= 2.0;  // the doubling is exact: the same as doubling each term
     return true;
