@@ -159,9 +159,9 @@ sphx_status sphx_intersect_gca_constlat_adaptive(const double *A, const double *
    pointers, best page-locked). When all five are page-locked memory the device
    maps (unified addressing; over NVLink-C2C on GB300), the kernel reads and
    writes them in place, with no staging copies. Otherwise the arcs go through
-   the context's device staging in three chunks (of at most 524288 arcs; more
+   the context's device staging in four chunks (of at most 2097152 arcs; more
    chunks beyond that), each on its own stream of the context, so that the
-   copies in both directions overlap the kernels. The staging (156 B per arc of a chunk, per
+   copies in both directions overlap the kernels. The staging (108 B per arc of a chunk, per
    stream) is allocated when a call needs more than the last and kept.
    The work starts after the work already enqueued on `stream` but does not
    hold `stream` back: successive calls on one context overlap (one call's

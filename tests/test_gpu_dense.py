@@ -313,14 +313,14 @@ def test_full_size_stress_workload_sampled():
     assert np.array_equal(cd, cr) and P.same_bits(pd, pr)
 
 
-@pytest.mark.parametrize("n", [1, 1_000, 393_217, 1_572_865])
+@pytest.mark.parametrize("n", [1, 1_000, 393_217, 1_572_865, 8_519_681])
 @pytest.mark.parametrize("pinned", ["all", "none", "inputs"])
 def test_host_buffer_call_equals_device_call(n, pinned):
     """sphx_intersect_gca_constlat_host: with every buffer page-locked the
     kernel works on host memory in place; otherwise (pageable, or only the
-    inputs page-locked) three chunks (more past 3 x 2^19 arcs) go through the
-    context's staging. Identical results to the device-buffer call either way,
-    uneven chunks included."""
+    inputs page-locked) four chunks (more past 4 x 2^21 arcs: 8 519 681 takes
+    five, the last one short) go through the context's staging. Identical
+    results to the device-buffer call either way, uneven chunks included."""
     A, B, z = W.stress_arcs(n, seed=50 + n % 7)
     cnt_d, pts_d = run(A, B, z, "wide")
     hA, hB, hz = (torch.from_numpy(np.ascontiguousarray(v)) for v in (A, B, z))
