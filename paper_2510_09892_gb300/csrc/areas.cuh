@@ -72,8 +72,18 @@ EFT_HD bool node_at(const Mesh &m, int64_t i, double (&v)[3]) {
     return true;
 }
 
+// v / |v|. Mesh nodes are nearly always unit vectors to rounding, q = |v|^2 =
+// 1 + d with |d| of a few ulps: then 1 / sqrt(q) = 1 - d/2 + 3 d^2/8 - ..., to
+// d^2 (the next term is below 2^-61 for |d| <= 2^-20), takes two FMAs in place
+// of the reciprocal square root's sequence on the FP64 pipe
 EFT_HD void unit(const double (&v)[3], double (&u)[3]) {
-    const double r = rsqrt_hd(fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2])));
+    const double q = fma(v[0], v[0], fma(v[1], v[1], v[2] * v[2]));
+    const double d = q - 1.0;
+    double r;
+    if ((wide::bits_of(d) & 0x7fffffffffffffffull) <= 0x3eb0000000000000ull)  // |d| <= 2^-20
+        r = fma(d, fma(0.375, d, -0.5), 1.0);
+    else
+        r = rsqrt_hd(q);
     u[0] = v[0] * r;
     u[1] = v[1] * r;
     u[2] = v[2] * r;
@@ -120,6 +130,17 @@ EFT_HD double rho_of_lat(double z) { return sqrt((1.0 - z) * (1.0 + z)); }
 // small angle is accurate relative to itself
 EFT_HD double delta_lon(double rx, double ry, double x, double y) {
     return atan2(rx * (y - ry) - ry * (x - rx), fma(rx, x, ry * y));
+}
+
+// 1 / den for den in [1, 4], the Van Oosterom-Strackee denominators of the
+// fan triangles here (both apex dot products at least 1/2): an FP32 seed
+// (relative error below 2^-23) and two Newton steps in FP64 (2^-46, then the
+// rounding of the last step), four FMAs in place of a division's longer
+// sequence on the FP64 pipe
+EFT_HD double rcp_den(double den) {
+    const double r0 = f64_of_f32_small(wide::rcp32(f32_of(den)));
+    const double r1 = fma(r0, fma(-den, r0, 1.0), r0);
+    return fma(r1, fma(-den, r1, 1.0), r1);
 }
 
 // arctan x by its series x - x^3/3 + x^5/5 - x^7/7, for |x| <= 2^-9
@@ -361,7 +382,7 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
                 const double tri = fma(v0[0], d1y * d2z - d1z * d2y,
                                        fma(v0[1], d1z * d2x - d1x * d2z,
                                            v0[2] * (d1x * d2y - d1y * d2x)));
-                const double t = tri / (1.0 + oa + ab + ob);
+                const double t = tri * rcp_den(1.0 + oa + ab + ob);
                 area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
                 a[0] = b[0];
                 a[1] = b[1];
@@ -398,7 +419,7 @@ EFT_HD bool fan_of(const double (*p)[3], int n, double &area) {
         const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
         const double tri = fma(o[0], d1y * d2z - d1z * d2y,
                                fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
-        const double t = tri / (1.0 + oa + ab + ob);
+        const double t = tri * rcp_den(1.0 + oa + ab + ob);
         area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
         oa = ob;
         d1x = d2x;

@@ -252,3 +252,19 @@ extern "C" long long h_f32_of_mismatches(const double *x, long long n) {
     }
     return bad;
 }
+
+// the fan triangles' reciprocal (areas.cuh) and the nodes' normalisation
+extern "C" void h_rcp_den(const double *x, long long n, double *out) {
+    for (long long i = 0; i < n; ++i) out[i] = sphx::rcp_den(x[i]);
+}
+
+extern "C" void h_unit(const double *v, long long n, double *out) {
+    for (long long i = 0; i < n; ++i) {
+        const double a[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+        double u[3];
+        sphx::unit(a, u);
+        out[3 * i] = u[0];
+        out[3 * i + 1] = u[1];
+        out[3 * i + 2] = u[2];
+    }
+}

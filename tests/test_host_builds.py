@@ -209,6 +209,8 @@ def pair_lib():
     L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
     L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
     L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp, vp]
+    L.h_rcp_den.argtypes = [vp, ll, vp]
+    L.h_unit.argtypes = [vp, ll, vp]
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
     L.h_from_fixed.argtypes = [vp, vp, ll, vp]
@@ -522,6 +524,45 @@ def test_fp32_height_range_refuses_non_finite_endpoints(pair_lib):
     finite = np.isfinite(A).all(1) & np.isfinite(B).all(1)
     assert not ok[bad][~finite[bad]].any()
     assert f32[n - len(A0):].all() and ok[n - len(A0):].all()
+
+
+def test_fan_reciprocal_and_node_normalisation_on_the_host(pair_lib):
+    """The area kernels' two FP64 shortcuts, against exact rationals (the
+    reciprocal) and 200-bit arithmetic (the normalisation): the
+    reciprocal of a fan triangle's denominator (FP32 seed, two Newton steps)
+    within 1 ulp of 1/den over [1, 4] (random values, the ends, powers of two
+    and their neighbours), and the normalisation of nodes whose squared norm is
+    within 2^-20 of 1 (the series branch) as well as of others (the reciprocal
+    square root), within 4 units of 2^-53 of the exact v / |v|, relative, per
+    component."""
+    import numpy as np
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(109)
+    x = np.concatenate([rng.uniform(1.0, 4.0, 4000), [1.0, 2.0, 4.0, 3.0, 1.5],
+                        np.nextafter([1.0, 2.0, 2.0, 4.0], [2.0, 1.0, 3.0, 3.0])])
+    out = np.empty_like(x)
+    pair_lib.h_rcp_den(x.ctypes.data, len(x), out.ctypes.data)
+    err = np.array([abs(Fr(float(o)) - 1 / Fr(float(v))) / (1 / Fr(float(v))) for v, o in zip(x, out)],
+                   dtype=float)
+    assert err.max() <= 2.0 ** -52
+    # nodes: unit to rounding, scaled by 1 + up to 2^-21 (series), and far from unit
+    v = rng.standard_normal((3000, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    scale = np.concatenate([np.ones(1000), 1 + rng.uniform(-2.0 ** -22, 2.0 ** -22, 1000),
+                            10.0 ** rng.uniform(-3, 3, 1000)])
+    v = np.ascontiguousarray(v * scale[:, None])
+    u = np.empty_like(v)
+    pair_lib.h_unit(v.ctypes.data, len(v), u.ctypes.data)
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 200
+    worst = 0.0
+    for i in range(len(v)):
+        r = 1 / mp.sqrt(sum(mp.mpf(float(c)) ** 2 for c in v[i]))
+        for k in range(3):
+            e = mp.mpf(float(v[i, k])) * r
+            if e != 0:
+                worst = max(worst, float(abs(mp.mpf(float(u[i, k])) - e) / abs(e)))
+    assert worst <= 4 * 2.0 ** -53
 
 
 def test_latitude_searches_on_the_host(pair_lib):
