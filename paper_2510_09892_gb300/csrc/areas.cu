@@ -166,6 +166,22 @@ __global__ void __launch_bounds__(kAreaThreads, 8)
     }
 }
 
+// every node as a unit vector (unit(): the same arithmetic the area routines
+// apply to a node when they read it), once per node instead of once per cell
+// that uses the node
+__global__ void unit_nodes_kernel(const double *__restrict__ nodes, int64_t n,
+                                  double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v[3] = {nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2]};
+        double u[3];
+        unit(v, u);
+        out[3 * i] = u[0];
+        out[3 * i + 1] = u[1];
+        out[3 * i + 2] = u[2];
+    }
+}
+
 // pair_area over the two-band list; a cell it does not cover is appended to
 // the other list (taken by band_area_kernel, launched after this kernel)
 template <int Mode>
@@ -410,8 +426,15 @@ extern "C" sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, i
     SPHX_CUDA(cudaSetDevice(ctx->device));
     sphx_status st = ensure_band_scratch(ctx, n_faces);
     if (st != SPHX_OK) return st;
-    const Mesh m =
+    if ((st = ensure_unit_nodes(ctx, n_nodes)) != SPHX_OK) return st;
+    Mesh m =
         make_mesh(ctx, nodes, n_nodes, face_offsets, face_nodes, n_face_nodes, n_faces, lat_z, n_lat);
+    if (n_nodes > 0) {
+        const int64_t grid = std::min<int64_t>((n_nodes + 255) / 256, (int64_t)ctx->sm_count * 8);
+        unit_nodes_kernel<<<(unsigned)grid, 256, 0, s>>>(nodes, n_nodes, ctx->unit_nodes);
+        SPHX_CUDA(cudaGetLastError());
+    }
+    m.unit_nodes = ctx->unit_nodes;
     const long long *off = reinterpret_cast<const long long *>(area_offsets);
     cudaError_t e;
     switch (mode) {

@@ -44,6 +44,10 @@ struct Mesh {
     const double *lat;
     int64_t L;
     unsigned *status;
+    // the nodes normalised by unit(), one vector per node, when the call made
+    // that copy (unit_nodes_kernel); else the routines normalise each node of
+    // a cell as they read it
+    const double *unit_nodes = nullptr;
 };
 
 // node range [s, e) of cell f in face_nodes; false (status flagged) if invalid
@@ -87,6 +91,42 @@ EFT_HD void unit(const double (&v)[3], double (&u)[3]) {
     u[0] = v[0] * r;
     u[1] = v[1] * r;
     u[2] = v[2] * r;
+}
+
+// node face_nodes[i] as a unit vector, given its coordinates `raw` as read
+// by node_at (which checked the index): from the normalised copy when there is
+// one (the same bits: unit() of the same node), else normalised here
+EFT_HD void unit_of(const Mesh &m, int64_t i, const double (&raw)[3], double (&u)[3]) {
+    if (m.unit_nodes) {
+        const double *p = m.unit_nodes + 3 * (int64_t)m.face_nodes[i];
+        u[0] = p[0];
+        u[1] = p[1];
+        u[2] = p[2];
+    } else {
+        unit(raw, u);
+    }
+}
+
+// node face_nodes[i] as a unit vector, for the routines that need no raw
+// coordinates (the fans); false (status flagged) for an index outside the
+// node array
+EFT_HD bool unit_node_at(const Mesh &m, int64_t i, double (&u)[3]) {
+    if (m.unit_nodes) {
+        const int32_t id = m.face_nodes[i];
+        if (id < 0 || (int64_t)id >= m.n_nodes) {
+            flag_status(m.status, kStatusInvalid);
+            return false;
+        }
+        const double *p = m.unit_nodes + 3 * (int64_t)id;
+        u[0] = p[0];
+        u[1] = p[1];
+        u[2] = p[2];
+        return true;
+    }
+    double raw[3];
+    if (!node_at(m, i, raw)) return false;
+    unit(raw, u);
+    return true;
 }
 
 // a point of an arc with what the boundary integral needs
@@ -143,10 +183,13 @@ EFT_HD double rcp_den(double den) {
     return fma(r1, fma(-den, r1, 1.0), r1);
 }
 
-// arctan x by its series x - x^3/3 + x^5/5 - x^7/7, for |x| <= 2^-9
-// (the next term is below 2^-84 |x|)
+// arctan x by its series x - x^3/3 + x^5/5 - x^7/7, for |x| <= 2^-9 (the
+// next term, x^9/9, is below 2^-75 |x|); for |x| <= 2^-18 (the triangles of
+// cells below about 0.1 degree) by x - x^3/3 alone (x^5/5 is below 2^-74 |x|)
 EFT_HD double atan_small(double x) {
     const double x2 = x * x;
+    if ((wide::bits_of(x) & 0x7fffffffffffffffull) <= 0x3ed0000000000000ull)  // |x| <= 2^-18
+        return fma(x * x2, -1.0 / 3.0, x);
     return fma(x * x2, fma(x2, fma(x2, -1.0 / 7.0, 1.0 / 5.0), -1.0 / 3.0), x);
 }
 
@@ -283,7 +326,7 @@ EFT_HD void green_cell(const Mesh &m, int64_t f,
     double a[3], ua[3];
     for (int64_t i = 0; i < nv; ++i) {
         if (!node_at(m, s + i, a)) break;
-        unit(a, ua);
+        unit_of(m, s + i, a, ua);
         if (!(fma(ua[0], ua[0], ua[1] * ua[1]) < kPoleRho * kPoleRho)) {
             st = i;
             break;
@@ -300,7 +343,7 @@ EFT_HD void green_cell(const Mesh &m, int64_t f,
         if (ib >= nv) ib -= nv;
         double b[3], ub[3];
         if (!(ok = node_at(m, s + ib, b))) break;
-        unit(b, ub);
+        unit_of(m, s + ib, b, ub);
         const Pt pb = make_pt(ub[0], ub[1], ub[2]);
         const bool a_pole = pa.rho == 0.0, b_pole = pb.rho == 0.0;
         if (a_pole && b_pole) {
@@ -359,22 +402,19 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
         }
         int64_t s, e;
         if (!cell_span(m, f, s, e)) return false;
-        double v0[3], a[3], b[3], u[3];
+        double v0[3] = {0.0, 0.0, 0.0}, a[3] = {0.0, 0.0, 0.0}, b[3];
         double area = 0.0;
         bool ok = true, far = false;
         if (e - s >= 3) {
-            ok = node_at(m, s, u);
-            unit(u, v0);
-            if (ok) ok = node_at(m, s + 1, u);
-            unit(u, a);
+            ok = unit_node_at(m, s, v0);
+            if (ok) ok = unit_node_at(m, s + 1, a);
             // node 0's dot product with a and the difference a - node 0 carry
             // over from one triangle to the next (b becomes a)
             double oa = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2]));
             double d1x = a[0] - v0[0], d1y = a[1] - v0[1], d1z = a[2] - v0[2];
             far = oa < 0.5;
             for (int64_t j = s + 2; j < e && ok && !far; ++j) {
-                if (!(ok = node_at(m, j, u))) break;
-                unit(u, b);
+                if (!(ok = unit_node_at(m, j, b))) break;
                 const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
                 const double ob = fma(v0[0], b[0], fma(v0[1], b[1], v0[2] * b[2]));
                 far = ob < 0.5;
@@ -466,7 +506,7 @@ EFT_HD bool pair_area(const Mesh &m, int64_t f,
     double v[kPairMaxNodes][3];  // the nodes, unit length
     for (int i = 0; i < nv; ++i) {
         if (!node_at(m, s + i, r[i])) return false;
-        unit(r[i], v[i]);
+        unit_of(m, s + i, r[i], v[i]);
     }
     // the arcs whose widened height range reaches z (only they can cross it);
     // evaluated in a loop over this mask, so that a warp runs as many

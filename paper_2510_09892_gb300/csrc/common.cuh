@@ -167,6 +167,8 @@ struct sphx_context {
     int64_t band_faces = 0;                // cells these buffers serve
     unsigned long long *zonal_acc = nullptr;  // zonal sums: 4 words per band
     int64_t zonal_bands = 0;
+    double *unit_nodes = nullptr;  // band areas: the mesh nodes normalised (3 x unit_node_cap)
+    int64_t unit_node_cap = 0;
     std::mutex mu;
 };
 
@@ -174,4 +176,5 @@ namespace sphx {
 // runtime.cu: per-context scratch of the band-area calls (grown on demand)
 sphx_status ensure_band_scratch(sphx_context *ctx, int64_t faces);
 sphx_status ensure_zonal_scratch(sphx_context *ctx, int64_t bands);
+sphx_status ensure_unit_nodes(sphx_context *ctx, int64_t nodes);
 }  // namespace sphx

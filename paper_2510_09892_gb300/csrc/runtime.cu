@@ -266,6 +266,22 @@ sphx_status sphx::ensure_band_scratch(sphx_context *ctx, int64_t faces) {
     return SPHX_OK;
 }
 
+sphx_status sphx::ensure_unit_nodes(sphx_context *ctx, int64_t nodes) {
+    if (ctx->unit_nodes && ctx->unit_node_cap >= nodes) return SPHX_OK;
+    SPHX_CUDA(cudaDeviceSynchronize());  // nothing may still use the old buffer
+    cudaFree(ctx->unit_nodes);
+    ctx->unit_nodes = nullptr;
+    ctx->unit_node_cap = 0;
+    const int64_t cap = nodes + nodes / 4 + 1024;
+    if (cudaMalloc(&ctx->unit_nodes, 3 * cap * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->unit_nodes = nullptr;
+        return SPHX_ERR_NOMEM;
+    }
+    ctx->unit_node_cap = cap;
+    return SPHX_OK;
+}
+
 sphx_status sphx::ensure_zonal_scratch(sphx_context *ctx, int64_t bands) {
     if (ctx->zonal_acc && ctx->zonal_bands >= bands) return SPHX_OK;
     SPHX_CUDA(cudaDeviceSynchronize());
@@ -600,6 +616,7 @@ void sphx_destroy(sphx_context *ctx) {
     cudaFree(ctx->band_lists);
     cudaFree(ctx->band_counts);
     cudaFree(ctx->zonal_acc);
+    cudaFree(ctx->unit_nodes);
     cudaFree(ctx->status);
     cudaStreamDestroy(ctx->capture_stream);
     delete ctx;

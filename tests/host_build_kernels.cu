@@ -121,16 +121,33 @@ extern "C" void h_pair_filtered(const double *A, const double *B, const double *
     }
 }
 
+// the normalised copy of the nodes that sphx_band_areas makes (unit() per
+// node), or nullptr: the area routines must give the same bits either way
+static double *unit_copy(const double *nodes, long long n_nodes, int pre) {
+    if (!pre) return nullptr;
+    double *u = new double[3 * (n_nodes > 0 ? n_nodes : 1)];
+    for (long long i = 0; i < n_nodes; ++i) {
+        const double v[3] = {nodes[3 * i], nodes[3 * i + 1], nodes[3 * i + 2]};
+        double w[3];
+        sphx::unit(v, w);
+        u[3 * i] = w[0];
+        u[3 * i + 1] = w[1];
+        u[3 * i + 2] = w[2];
+    }
+    return u;
+}
+
 // band areas of every cell with the boundary integral (green_cell, crossings
 // in integer limbs), each cell given the full band range: out is n_faces x
 // (L - 1), row f the areas of cell f in bands 0 .. L - 2
 extern "C" unsigned h_green_cells(const double *nodes, long long n_nodes,
                                   const long long *face_offsets, const int *face_nodes,
                                   long long n_faces, const double *lat, long long L,
-                                  double *out) {
+                                  double *out, int pre) {
     unsigned status = 0u;
+    double *un = unit_copy(nodes, n_nodes, pre);
     sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
-                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status};
+                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status, un};
     const long long nb = L - 1;
     int32_t *lo = new int32_t[n_faces], *hi = new int32_t[n_faces];
     long long *off = new long long[n_faces];
@@ -143,6 +160,7 @@ extern "C" unsigned h_green_cells(const double *nodes, long long n_nodes,
     }
     for (long long f = 0; f < n_faces; ++f)
         sphx::green_cell<sphx::kWideInt>(m, f, lo, hi, off, out, n_faces * nb, lat, rho);
+    delete[] un;
     delete[] lo;
     delete[] hi;
     delete[] off;
@@ -153,16 +171,18 @@ extern "C" unsigned h_green_cells(const double *nodes, long long n_nodes,
 // the fan area of every cell (fan_area): area[f], or NaN where the routine
 // declines the cell (a node more than 60 degrees from node 0)
 extern "C" void h_fan_cells(const double *nodes, long long n_nodes, const long long *face_offsets,
-                            const int *face_nodes, long long n_faces, double *area) {
+                            const int *face_nodes, long long n_faces, double *area, int pre) {
     unsigned status = 0u;
+    double *un = unit_copy(nodes, n_nodes, pre);
     sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
-                 (int64_t)face_offsets[n_faces], n_faces, nullptr, 0, &status};
+                 (int64_t)face_offsets[n_faces], n_faces, nullptr, 0, &status, un};
     long long *off = new long long[n_faces];
     for (long long f = 0; f < n_faces; ++f) {
         off[f] = f;
         area[f] = __builtin_nan("");
     }
     for (long long f = 0; f < n_faces; ++f) sphx::fan_area(m, f, off, area, n_faces);
+    delete[] un;
     delete[] off;
 }
 
@@ -172,10 +192,11 @@ extern "C" void h_fan_cells(const double *nodes, long long n_nodes, const long l
 extern "C" void h_pair_cells(const double *nodes, long long n_nodes,
                              const long long *face_offsets, const int *face_nodes,
                              long long n_faces, const double *lat, long long L,
-                             const int *band_lo, double *out) {
+                             const int *band_lo, double *out, int pre) {
     unsigned status = 0u;
+    double *un = unit_copy(nodes, n_nodes, pre);
     sphx::Mesh m{nodes, n_nodes, (const int64_t *)face_offsets, face_nodes,
-                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status};
+                 (int64_t)face_offsets[n_faces], n_faces, lat, L, &status, un};
     long long *off = new long long[n_faces];
     for (long long f = 0; f < n_faces; ++f) {
         off[f] = 2 * f;
@@ -183,6 +204,7 @@ extern "C" void h_pair_cells(const double *nodes, long long n_nodes,
     }
     for (long long f = 0; f < n_faces; ++f)
         sphx::pair_area<sphx::kWideInt>(m, f, band_lo, off, out, 2 * n_faces, lat);
+    delete[] un;
     delete[] off;
 }
 

@@ -204,10 +204,10 @@ def pair_lib():
     vp, ll = ctypes.c_void_p, ctypes.c_longlong
     L.h_f32_of_mismatches.argtypes = [vp, ll]
     L.h_f32_of_mismatches.restype = ll
-    L.h_green_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp]
+    L.h_green_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, ctypes.c_int]
     L.h_green_cells.restype = ctypes.c_uint
-    L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp]
-    L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp]
+    L.h_fan_cells.argtypes = [vp, ll, vp, vp, ll, vp, ctypes.c_int]
+    L.h_pair_cells.argtypes = [vp, ll, vp, vp, ll, vp, ll, vp, vp, ctypes.c_int]
     L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp, vp]
     L.h_rcp_den.argtypes = [vp, ll, vp]
     L.h_unit.argtypes = [vp, ll, vp]
@@ -410,7 +410,9 @@ def _area_tolerance(cells):
 @pytest.mark.parametrize("kind", ["polygons", "cubed_sphere"])
 def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
     """The boundary integral on every cell; the fan on the cells the oracle puts
-    inside one interior band; the fan plus sliver on the cells it puts in two."""
+    inside one interior band; the fan plus sliver on the cells it puts in two.
+    Each routine gives the same bits whether it normalises the nodes itself or
+    reads the normalised copy that sphx_band_areas makes once per node."""
     import numpy as np
     from oracle import areas as OA
     from paper_2510_09892_gb300 import workloads as W
@@ -429,8 +431,11 @@ def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
     tol = _area_tolerance(cells)
     args = (nodes.ctypes.data, len(nodes), off.ctypes.data, fn.ctypes.data, F)
     green = np.zeros((F, nb))
-    st = pair_lib.h_green_cells(*args, lat.ctypes.data, len(lat), green.ctypes.data)
+    st = pair_lib.h_green_cells(*args, lat.ctypes.data, len(lat), green.ctypes.data, 0)
     assert st == 0
+    green_pre = np.zeros((F, nb))
+    assert pair_lib.h_green_cells(*args, lat.ctypes.data, len(lat), green_pre.ctypes.data, 1) == 0
+    assert np.array_equal(green, green_pre)
     assert (np.abs(green - ref) <= tol[:, None]).all(), (np.abs(green - ref) / tol[:, None]).max()
     # cells in one / two interior bands (by the oracle)
     inside = ref > tol[:, None]
@@ -441,13 +446,19 @@ def test_band_area_routines_on_the_host_match_oracle(pair_lib, kind):
     next_band = inside[np.arange(F), np.minimum(first + 1, nb - 1)]
     two = np.flatnonzero((nbands == 2) & interior & next_band)
     fan = np.empty(F)
-    pair_lib.h_fan_cells(*args, fan.ctypes.data)
+    pair_lib.h_fan_cells(*args, fan.ctypes.data, 0)
+    fan_pre = np.empty(F)
+    pair_lib.h_fan_cells(*args, fan_pre.ctypes.data, 1)
+    assert np.array_equal(fan, fan_pre, equal_nan=True)
     done = one[np.isfinite(fan[one])]
     assert len(one) > 0 and len(done) >= 0.5 * len(one)
     assert (np.abs(fan[done] - ref[done].sum(axis=1)) <= tol[done]).all()
     lo = first.astype(np.int32)
     pr = np.empty(2 * F)
-    pair_lib.h_pair_cells(*args, lat.ctypes.data, len(lat), lo.ctypes.data, pr.ctypes.data)
+    pair_lib.h_pair_cells(*args, lat.ctypes.data, len(lat), lo.ctypes.data, pr.ctypes.data, 0)
+    pr_pre = np.empty(2 * F)
+    pair_lib.h_pair_cells(*args, lat.ctypes.data, len(lat), lo.ctypes.data, pr_pre.ctypes.data, 1)
+    assert np.array_equal(pr, pr_pre, equal_nan=True)
     pr = pr.reshape(F, 2)
     done2 = two[np.isfinite(pr[two, 0])]
     assert len(two) > 0 and len(done2) >= 0.5 * len(two)
