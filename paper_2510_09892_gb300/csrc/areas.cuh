@@ -172,6 +172,23 @@ EFT_HD double delta_lon(double rx, double ry, double x, double y) {
     return atan2(rx * (y - ry) - ry * (x - rx), fma(rx, x, ry * y));
 }
 
+// Comparisons of a double with a constant on the integer pipe (GB300 runs
+// FP64 instructions, comparisons included, at 2 per SM per clock), each with
+// the FP64 comparison's result for every input, NaN and signed zero included.
+// x < c for a constant c > 0 (cbits = the bits of c)
+EFT_HD bool lt_pos(double x, uint64_t cbits) {
+    const uint64_t b = wide::bits_of(x);
+    return (b >> 63) ? ((b & 0x7fffffffffffffffull) <= 0x7ff0000000000000ull) : (b < cbits);
+}
+// |x| <= c for a constant c > 0
+EFT_HD bool abs_le(double x, uint64_t cbits) {
+    return (wide::bits_of(x) & 0x7fffffffffffffffull) <= cbits;
+}
+// x > 0
+EFT_HD bool gt_zero(double x) { return wide::bits_of(x) - 1u < 0x7ff0000000000000ull; }
+constexpr uint64_t kBitsHalf = 0x3fe0000000000000ull;    // 0.5
+constexpr uint64_t kBitsSeries = 0x3f60000000000000ull;  // 2^-9
+
 // 1 / den for den in [1, 4], the Van Oosterom-Strackee denominators of the
 // fan triangles here (both apex dot products at least 1/2): an FP32 seed
 // (relative error below 2^-23) and two Newton steps in FP64 (2^-46, then the
@@ -412,18 +429,18 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
             // over from one triangle to the next (b becomes a)
             double oa = fma(v0[0], a[0], fma(v0[1], a[1], v0[2] * a[2]));
             double d1x = a[0] - v0[0], d1y = a[1] - v0[1], d1z = a[2] - v0[2];
-            far = oa < 0.5;
+            far = lt_pos(oa, kBitsHalf);
             for (int64_t j = s + 2; j < e && ok && !far; ++j) {
                 if (!(ok = unit_node_at(m, j, b))) break;
                 const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
                 const double ob = fma(v0[0], b[0], fma(v0[1], b[1], v0[2] * b[2]));
-                far = ob < 0.5;
+                far = lt_pos(ob, kBitsHalf);
                 const double d2x = b[0] - v0[0], d2y = b[1] - v0[1], d2z = b[2] - v0[2];
                 const double tri = fma(v0[0], d1y * d2z - d1z * d2y,
                                        fma(v0[1], d1z * d2x - d1x * d2z,
                                            v0[2] * (d1x * d2y - d1y * d2x)));
                 const double t = tri * rcp_den(1.0 + oa + ab + ob);
-                area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
+                area += abs_le(t, kBitsSeries) ? atan_small(t) : atan(t);  // half the excess
                 a[0] = b[0];
                 a[1] = b[1];
                 a[2] = b[2];
@@ -450,17 +467,17 @@ EFT_HD bool fan_of(const double (*p)[3], int n, double &area) {
     // from one triangle to the next
     double oa = fma(o[0], p[1][0], fma(o[1], p[1][1], o[2] * p[1][2]));
     double d1x = p[1][0] - o[0], d1y = p[1][1] - o[1], d1z = p[1][2] - o[2];
-    if (oa < 0.5) return false;
+    if (lt_pos(oa, kBitsHalf)) return false;
     for (int i = 1; i + 1 < n; ++i) {
         const double *a = p[i], *b = p[i + 1];
         const double ob = fma(o[0], b[0], fma(o[1], b[1], o[2] * b[2]));
         const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
-        if (ob < 0.5) return false;
+        if (lt_pos(ob, kBitsHalf)) return false;
         const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
         const double tri = fma(o[0], d1y * d2z - d1z * d2y,
                                fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
         const double t = tri * rcp_den(1.0 + oa + ab + ob);
-        area += fabs(t) <= 0.001953125 ? atan_small(t) : atan(t);  // half the excess
+        area += abs_le(t, kBitsSeries) ? atan_small(t) : atan(t);  // half the excess
         oa = ob;
         d1x = d2x;
         d1y = d2y;
@@ -583,10 +600,10 @@ EFT_HD bool pair_area(const Mesh &m, int64_t f,
     const double cr = Pd[0] * (Pu[1] - Pd[1]) - Pd[1] * (Pu[0] - Pd[0]);
     const double rho2 = (1.0 - z) * (1.0 + z);
     const double den = rho2 + fma(Pd[0], Pu[0], Pd[1] * Pu[1]);
-    if (!(cr > 0.0) || !(den > 0.0)) return true;  // P_u must lie east of P_d, within pi
+    if (!gt_zero(cr) || !gt_zero(den)) return true;  // P_u must lie east of P_d, within pi
     const double t = cr / den;
     double sliver;
-    if (t <= 0.001953125) {
+    if (abs_le(t, kBitsSeries)) {  // t > 0 here
         const double z2 = z * z, t2 = t * t;
         // the coefficients' divisions by 7 and 5 as products with the
         // constants' reciprocals (an FP64 division costs several FMAs)

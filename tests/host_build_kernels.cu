@@ -290,3 +290,11 @@ extern "C" void h_unit(const double *v, long long n, double *out) {
         out[3 * i + 2] = u[2];
     }
 }
+
+// the area routines' integer-pipe comparisons: bit 0 lt_pos(x, 0.5), bit 1
+// abs_le(x, 2^-9), bit 2 gt_zero(x)
+extern "C" void h_compares(const double *x, long long n, int *out) {
+    for (long long i = 0; i < n; ++i)
+        out[i] = (sphx::lt_pos(x[i], sphx::kBitsHalf) ? 1 : 0) |
+                 (sphx::abs_le(x[i], sphx::kBitsSeries) ? 2 : 0) | (sphx::gt_zero(x[i]) ? 4 : 0);
+}

@@ -211,6 +211,7 @@ def pair_lib():
     L.h_z_ranges.argtypes = [vp, vp, ll, vp, vp, vp, vp]
     L.h_rcp_den.argtypes = [vp, ll, vp]
     L.h_unit.argtypes = [vp, ll, vp]
+    L.h_compares.argtypes = [vp, ll, vp]
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
     L.h_from_fixed.argtypes = [vp, vp, ll, vp]
@@ -574,6 +575,29 @@ def test_fan_reciprocal_and_node_normalisation_on_the_host(pair_lib):
             if e != 0:
                 worst = max(worst, float(abs(mp.mpf(float(u[i, k])) - e) / abs(e)))
     assert worst <= 4 * 2.0 ** -53
+
+
+def test_integer_comparisons_equal_the_fp64_ones(pair_lib):
+    """The area routines compare doubles with constants on the integer pipe:
+    x < 0.5, |x| <= 2^-9 and x > 0 must equal the FP64 comparisons for signed
+    zeros, subnormals, the constants and their neighbours, infinities, NaNs of
+    either sign and random doubles over the whole exponent range."""
+    import numpy as np
+    rng = np.random.default_rng(110)
+    special = [0.0, -0.0, 5e-324, -5e-324, 0.5, -0.5, 2.0 ** -9, -(2.0 ** -9),
+               np.inf, -np.inf, np.nan, -np.nan, 1.0, -1.0, 1e308, -1e308]
+    special += list(np.nextafter([0.5, 0.5, 2.0 ** -9, 2.0 ** -9], [0, 1, 0, 1]))
+    bits = rng.integers(0, 2 ** 63, 20000, dtype=np.uint64) | (
+        rng.integers(0, 2, 20000, dtype=np.uint64) << np.uint64(63))
+    x = np.ascontiguousarray(np.concatenate([np.array(special), bits.view(np.float64),
+                                             rng.uniform(-1, 1, 5000)]))
+    x[len(special) + 3] = np.frombuffer(np.uint64(0xfff8000000000001).tobytes(), np.float64)[0]
+    out = np.empty(len(x), dtype=np.int32)
+    pair_lib.h_compares(x.ctypes.data, len(x), out.ctypes.data)
+    with np.errstate(invalid="ignore"):
+        want = ((x < 0.5).astype(int) | ((np.abs(x) <= 2.0 ** -9).astype(int) << 1)
+                | ((x > 0.0).astype(int) << 2))
+    assert np.array_equal(out, want)
 
 
 def test_latitude_searches_on_the_host(pair_lib):
