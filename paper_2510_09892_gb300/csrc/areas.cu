@@ -183,9 +183,13 @@ __global__ void unit_nodes_kernel(const double *__restrict__ nodes, int64_t n,
 }
 
 // pair_area over the two-band list; a cell it does not cover is appended to
-// the other list (taken by band_area_kernel, launched after this kernel)
+// the other list (taken by band_area_kernel, launched after this kernel).
+// Four resident blocks per SM (at most 128 registers, a few bytes of spills):
+// its FP64 chains need the warps; measured on GB300 on the cubed sphere
+// N = 1024, 3.23 -> 3.02 ms for the whole band-area call against the
+// unbounded 146 registers (3 blocks); 5, 6 and 8 blocks gave the same 3.0 ms
 template <int Mode>
-__global__ void __launch_bounds__(kAreaThreads)
+__global__ void __launch_bounds__(kAreaThreads, 4)
     pair_area_kernel(Mesh m, const int32_t *__restrict__ band_lo,
                      const long long *__restrict__ offsets, double *__restrict__ areas, int64_t cap,
                      int32_t *__restrict__ lists, unsigned long long *__restrict__ counts) {

@@ -457,35 +457,54 @@ EFT_HD bool fan_area(const Mesh &m, int64_t f,
     }
 }
 
-// fan area of the points p[0..n) (unit vectors) from p[0]; false when a point
-// is more than 60 degrees from p[0]
-EFT_HD bool fan_of(const double (*p)[3], int n, double &area) {
-    area = 0.0;
-    if (n < 3) return true;
-    const double *o = p[0];
-    // p[0]'s dot product with p[i] and the difference p[i] - p[0] carry over
-    // from one triangle to the next
-    double oa = fma(o[0], p[1][0], fma(o[1], p[1][1], o[2] * p[1][2]));
-    double d1x = p[1][0] - o[0], d1y = p[1][1] - o[1], d1z = p[1][2] - o[2];
-    if (lt_pos(oa, kBitsHalf)) return false;
-    for (int i = 1; i + 1 < n; ++i) {
-        const double *a = p[i], *b = p[i + 1];
-        const double ob = fma(o[0], b[0], fma(o[1], b[1], o[2] * b[2]));
+// Fan area of a sequence of points (unit vectors) from its first, the apex,
+// accumulated one point at a time (the points need not sit in an array):
+// the same triangles, in the same order and arithmetic, as fan_area's loop.
+// ok turns false when a point of a triangle is more than 60 degrees from the
+// apex (a sequence of two points has no triangle and no such test).
+struct Fan {
+    double o[3], a[3];  // the apex and the last point added
+    double oa, d1[3];   // the apex's dot product with a, and a - apex
+    double half;        // sum of the triangles' half excesses
+    int n;              // points added after the apex
+    bool ok;
+};
+
+EFT_HD void fan_start(Fan &f, const double (&o)[3]) {
+    f.o[0] = o[0];
+    f.o[1] = o[1];
+    f.o[2] = o[2];
+    f.half = 0.0;
+    f.n = 0;
+    f.ok = true;
+}
+
+EFT_HD void fan_add(Fan &f, const double (&b)[3]) {
+    const double *o = f.o;
+    const double ob = fma(o[0], b[0], fma(o[1], b[1], o[2] * b[2]));
+    const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
+    if (f.n > 0) {
+        const double *a = f.a;
         const double ab = fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
-        if (lt_pos(ob, kBitsHalf)) return false;
-        const double d2x = b[0] - o[0], d2y = b[1] - o[1], d2z = b[2] - o[2];
+        if (lt_pos(f.oa, kBitsHalf) || lt_pos(ob, kBitsHalf)) f.ok = false;
+        const double d1x = f.d1[0], d1y = f.d1[1], d1z = f.d1[2];
         const double tri = fma(o[0], d1y * d2z - d1z * d2y,
                                fma(o[1], d1z * d2x - d1x * d2z, o[2] * (d1x * d2y - d1y * d2x)));
-        const double t = tri * rcp_den(1.0 + oa + ab + ob);
-        area += abs_le(t, kBitsSeries) ? atan_small(t) : atan(t);  // half the excess
-        oa = ob;
-        d1x = d2x;
-        d1y = d2y;
-        d1z = d2z;
+        const double t = tri * rcp_den(1.0 + f.oa + ab + ob);
+        f.half += abs_le(t, kBitsSeries) ? atan_small(t) : atan(t);
     }
-    area *= 2.0;  // the doubling is exact: the same as doubling each term
-    return true;
+    f.a[0] = b[0];
+    f.a[1] = b[1];
+    f.a[2] = b[2];
+    f.oa = ob;
+    f.d1[0] = d2x;
+    f.d1[1] = d2y;
+    f.d1[2] = d2z;
+    ++f.n;
 }
+
+// the fan's area (the doubling is exact: the same as doubling each term)
+EFT_HD double fan_area_of(const Fan &f) { return 2.0 * f.half; }
 
 constexpr int kPairMaxNodes = 16;  // cells with more nodes take the boundary integral
 
@@ -573,29 +592,21 @@ EFT_HD bool pair_area(const Mesh &m, int64_t f,
     }
     if (nu != 1 || nd != 1) return true;
     // the cell's own fan area
-    double total;
-    if (!fan_of(v, nv, total)) return true;
+    Fan fan;
+    fan_start(fan, v[0]);
+    for (int i = 1; i < nv; ++i) fan_add(fan, v[i]);
+    if (!fan.ok) return true;
+    const double total = fan_area_of(fan);
     // the part above z: P_u, the nodes after P_u's arc up to P_d's arc, P_d
-    double q[kPairMaxNodes + 2][3];
-    int nq = 0;
-    q[nq][0] = Pu[0];
-    q[nq][1] = Pu[1];
-    q[nq][2] = Pu[2];
-    ++nq;
-    int cnt = au == ad ? (up_first ? 0 : nv) : (ad - au + nv) % nv;
+    fan_start(fan, Pu);
+    const int cnt = au == ad ? (up_first ? 0 : nv) : (ad > au ? ad - au : ad - au + nv);
     for (int k = 1; k <= cnt; ++k) {
-        const int i = (au + k) % nv;
-        q[nq][0] = v[i][0];
-        q[nq][1] = v[i][1];
-        q[nq][2] = v[i][2];
-        ++nq;
+        const int i = au + k < nv ? au + k : au + k - nv;
+        fan_add(fan, v[i]);
     }
-    q[nq][0] = Pd[0];
-    q[nq][1] = Pd[1];
-    q[nq][2] = Pd[2];
-    ++nq;
-    double above;
-    if (!fan_of(q, nq, above)) return true;
+    fan_add(fan, Pd);
+    if (!fan.ok) return true;
+    double above = fan_area_of(fan);
     // the sliver between the chord P_d -> P_u and the latitude arc
     const double cr = Pd[0] * (Pu[1] - Pd[1]) - Pd[1] * (Pu[0] - Pd[0]);
     const double rho2 = (1.0 - z) * (1.0 + z);
