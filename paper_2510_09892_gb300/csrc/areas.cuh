@@ -184,8 +184,7 @@ EFT_HD bool lt_pos(double x, uint64_t cbits) {
 EFT_HD bool abs_le(double x, uint64_t cbits) {
     return (wide::bits_of(x) & 0x7fffffffffffffffull) <= cbits;
 }
-// x > 0
-EFT_HD bool gt_zero(double x) { return wide::bits_of(x) - 1u < 0x7ff0000000000000ull; }
+// (x > 0: gt_zero of intersect.cuh)
 constexpr uint64_t kBitsHalf = 0x3fe0000000000000ull;    // 0.5
 constexpr uint64_t kBitsSeries = 0x3f60000000000000ull;  // 2^-9
 

@@ -28,9 +28,23 @@ struct PairOut {
     double px[2], py[2];
 };
 
+// Tests of doubles on the integer pipe (GB300 issues FP64 instructions,
+// comparisons included, at 2 per SM per clock), each with the FP64 test's
+// result for every input: NaN compares false, -0 equals +0.
+SPHX_HD bool finite_bits(double x) {  // isfinite(x)
+    return ((wide::bits_of(x) >> 52) & 0x7ff) != 0x7ff;
+}
+SPHX_HD bool eq_zero(double x) { return (wide::bits_of(x) << 1) == 0; }  // x == 0
+SPHX_HD bool ge_zero(double x) {                                          // x >= 0
+    const uint64_t b = wide::bits_of(x);
+    return b <= 0x7ff0000000000000ull || b == 0x8000000000000000ull;
+}
+SPHX_HD bool gt_zero(double x) { return wide::bits_of(x) - 1u < 0x7ff0000000000000ull; }  // x > 0
+
 EFT_HD bool finite7(const double (&x1)[3], const double (&x2)[3], double z0) {
-    return isfinite(x1[0]) && isfinite(x1[1]) && isfinite(x1[2]) && isfinite(x2[0]) &&
-           isfinite(x2[1]) && isfinite(x2[2]) && isfinite(z0);
+    // bitwise &: one test of the seven exponent fields, no branch per value
+    return finite_bits(x1[0]) & finite_bits(x1[1]) & finite_bits(x1[2]) & finite_bits(x2[0]) &
+           finite_bits(x2[1]) & finite_bits(x2[2]) & finite_bits(z0);
 }
 
 SPHX_HD void clear(PairOut &o, int count) {
@@ -48,10 +62,10 @@ EFT_HD void pair_direct(const double (&x1)[3], const double (&x2)[3],
     double nz = sub(mul(x1[0], x2[1]), mul(x1[1], x2[0]));
     double S2 = add(mul(nx, nx), mul(ny, ny));
     double S3 = add(S2, mul(nz, nz));
-    if (S3 == 0.0) return clear(o, -1);
-    if (S2 == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
+    if (eq_zero(S3)) return clear(o, -1);
+    if (eq_zero(S2)) return clear(o, eq_zero(z0) ? -1 : 0);
     double s2 = sub(S2, mul(S3, mul(z0, z0)));
-    if (!(s2 >= 0.0)) return clear(o, 0);
+    if (!ge_zero(s2)) return clear(o, 0);
     double s = sqrt_(s2);
     double a = mul(mul(z0, nx), nz);
     double b = mul(mul(z0, ny), nz);
@@ -62,7 +76,7 @@ EFT_HD void pair_direct(const double (&x1)[3], const double (&x2)[3],
     double m2x = sub(mul(x2[1], nz), mul(x2[2], ny));
     double m2y = sub(mul(x2[2], nx), mul(x2[0], nz));
     double m2z = sub(mul(x2[0], ny), mul(x2[1], nx));
-    const int nroots = s2 > 0.0 ? 2 : 1;
+    const int nroots = gt_zero(s2) ? 2 : 1;
     o.count = 0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -76,7 +90,7 @@ EFT_HD void pair_direct(const double (&x1)[3], const double (&x2)[3],
         double t2 = add(add(mul(Px, m2x), mul(Py, m2y)), mul(z0, m2z));
         o.px[r] = Px;
         o.py[r] = Py;
-        if (t1 >= 0.0 && t2 >= 0.0) {
+        if (ge_zero(t1) && ge_zero(t2)) {
             o.hit[r] = true;
             ++o.count;
         }
@@ -117,8 +131,8 @@ EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
         mid[8] = S3;
         mid[9] = s3;
     }
-    if (S3 == 0.0) return clear(o, -1);
-    if (S2 == 0.0) return clear(o, z0 == 0.0 ? -1 : 0);
+    if (eq_zero(S3)) return clear(o, -1);
+    if (eq_zero(S2)) return clear(o, eq_zero(z0) ? -1 : 0);
     // s^2 = |n_xy|^2 - |n|^2 z0^2 as a pair
     double C, eC, D, eD, E, eE;
     two_prod(z0, z0, C, eC);
@@ -134,7 +148,7 @@ EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
         mid[10] = ss;
         mid[11] = ess;
     }
-    if (!(ss >= 0.0)) return clear(o, 0);
+    if (!ge_zero(ss)) return clear(o, 0);
     double sb, es;
     acc_sqrt(ss, ess, sb, es);
     if (mid) {
@@ -154,7 +168,7 @@ EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
     double m2x = fma_(x2[1], n[2], -mul(x2[2], n[1]));
     double m2y = fma_(x2[2], n[0], -mul(x2[0], n[2]));
     double m2z = fma_(x2[0], n[1], -mul(x2[1], n[0]));
-    const int nroots = ss > 0.0 ? 2 : 1;
+    const int nroots = gt_zero(ss) ? 2 : 1;
     o.count = 0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -174,7 +188,7 @@ EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
         double t2 = fma_(Px, m2x, fma_(Py, m2y, mul(z0, m2z)));
         o.px[r] = Px;
         o.py[r] = Py;
-        if (t1 >= 0.0 && t2 >= 0.0) {
+        if (ge_zero(t1) && ge_zero(t2)) {
             o.hit[r] = true;
             ++o.count;
         }
@@ -201,10 +215,6 @@ EFT_HD void pair_accux(const double (&x1)[3], const double (&x2)[3],
 // FP64 FMA per component) decide its sign correctly except within an angle
 // of about 2^-40 of the endpoint (the oracle's near-endpoint flag).
 // Likewise t2 = (P x x2).n = d2 . m2.
-
-SPHX_HD bool finite_bits(double x) {
-    return ((wide::bits_of(x) >> 52) & 0x7ff) != 0x7ff;
-}
 
 SPHX_HD int exponent_bits(double x) {  // unbiased; very small for 0
     const int ex = (int)((wide::bits_of(x) >> 52) & 0x7ff);
