@@ -76,11 +76,10 @@ struct ArcOut {
 
 SPHX_HD bool finite12(const double (&a1)[3], const double (&a2)[3], const double (&b1)[3],
                       const double (&b2)[3]) {
-    bool ok = true;
+    bool ok = true;  // bitwise &: one test of the twelve exponent fields
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        ok = ok && finite_bits(a1[i]) && finite_bits(a2[i]) && finite_bits(b1[i]) &&
-             finite_bits(b2[i]);
+        ok = ok & finite_bits(a1[i]) & finite_bits(a2[i]) & finite_bits(b1[i]) & finite_bits(b2[i]);
     return ok;
 }
 
@@ -157,8 +156,8 @@ __device__ __forceinline__ void arcs_eft(const double (&a1)[3], const double (&a
     accu_dop<double, true>(b1[1], b1[2], b2[1], b2[2], nb[0], eb[0]);
     accu_dop<double, true>(b1[2], b1[0], b2[2], b2[0], nb[1], eb[1]);
     accu_dop<double, true>(b1[0], b1[1], b2[0], b2[1], nb[2], eb[2]);
-    if ((na[0] == 0.0 && na[1] == 0.0 && na[2] == 0.0) ||
-        (nb[0] == 0.0 && nb[1] == 0.0 && nb[2] == 0.0)) {
+    if ((eq_zero(na[0]) && eq_zero(na[1]) && eq_zero(na[2])) ||
+        (eq_zero(nb[0]) && eq_zero(nb[1]) && eq_zero(nb[2]))) {
         clear(r.o, -1);
         return;
     }
@@ -170,7 +169,7 @@ __device__ __forceinline__ void arcs_eft(const double (&a1)[3], const double (&a
         const double ys[6] = {nb[k], eb[k], nb[k], nb[j], eb[j], nb[j]};
         v[i] = comp_dot<double, 6>(xs, ys);
     }
-    if (v[0] == 0.0 && v[1] == 0.0 && v[2] == 0.0) {
+    if (eq_zero(v[0]) && eq_zero(v[1]) && eq_zero(v[2])) {
         clear(r.o, -1);
         return;
     }
@@ -200,15 +199,15 @@ __device__ __forceinline__ void arcs_direct(const double (&a1)[3], const double 
     const double nb[3] = {sub(mul(b1[1], b2[2]), mul(b1[2], b2[1])),
                           sub(mul(b1[2], b2[0]), mul(b1[0], b2[2])),
                           sub(mul(b1[0], b2[1]), mul(b1[1], b2[0]))};
-    if ((na[0] == 0.0 && na[1] == 0.0 && na[2] == 0.0) ||
-        (nb[0] == 0.0 && nb[1] == 0.0 && nb[2] == 0.0)) {
+    if ((eq_zero(na[0]) && eq_zero(na[1]) && eq_zero(na[2])) ||
+        (eq_zero(nb[0]) && eq_zero(nb[1]) && eq_zero(nb[2]))) {
         clear(r.o, -1);
         return;
     }
     const double v[3] = {sub(mul(na[1], nb[2]), mul(na[2], nb[1])),
                          sub(mul(na[2], nb[0]), mul(na[0], nb[2])),
                          sub(mul(na[0], nb[1]), mul(na[1], nb[0]))};
-    if (v[0] == 0.0 && v[1] == 0.0 && v[2] == 0.0) {
+    if (eq_zero(v[0]) && eq_zero(v[1]) && eq_zero(v[2])) {
         clear(r.o, -1);
         return;
     }
@@ -229,8 +228,8 @@ __device__ __forceinline__ void arcs_direct(const double (&a1)[3], const double 
         const double m2 = sub(mul(u[0], w[1]), mul(u[1], w[0]));
         t[k] = add(add(mul(p[0], m0), mul(p[1], m1)), mul(p[2], m2));
     }
-    r.o.hit[0] = t[0] >= 0.0 && t[1] >= 0.0 && t[2] >= 0.0 && t[3] >= 0.0;
-    r.o.hit[1] = t[0] <= 0.0 && t[1] <= 0.0 && t[2] <= 0.0 && t[3] <= 0.0;
+    r.o.hit[0] = ge_zero(t[0]) && ge_zero(t[1]) && ge_zero(t[2]) && ge_zero(t[3]);
+    r.o.hit[1] = le_zero(t[0]) && le_zero(t[1]) && le_zero(t[2]) && le_zero(t[3]);
     r.o.count = (int)r.o.hit[0] + (int)r.o.hit[1];
     r.o.px[0] = p[0];
     r.o.py[0] = p[1];

@@ -40,6 +40,10 @@ SPHX_HD bool ge_zero(double x) {                                          // x >
     return b <= 0x7ff0000000000000ull || b == 0x8000000000000000ull;
 }
 SPHX_HD bool gt_zero(double x) { return wide::bits_of(x) - 1u < 0x7ff0000000000000ull; }  // x > 0
+SPHX_HD bool le_zero(double x) {                                          // x <= 0
+    const uint64_t b = wide::bits_of(x);
+    return b == 0u || (b >= 0x8000000000000000ull && b <= 0xfff0000000000000ull);
+}
 
 EFT_HD bool finite7(const double (&x1)[3], const double (&x2)[3], double z0) {
     // bitwise &: one test of the seven exponent fields, no branch per value

@@ -293,11 +293,11 @@ extern "C" void h_unit(const double *v, long long n, double *out) {
 
 // the integer-pipe tests of doubles: bit 0 lt_pos(x, 0.5), bit 1
 // abs_le(x, 2^-9), bit 2 gt_zero(x), bit 3 ge_zero(x), bit 4 eq_zero(x),
-// bit 5 finite_bits(x)
+// bit 5 finite_bits(x), bit 6 le_zero(x)
 extern "C" void h_compares(const double *x, long long n, int *out) {
     for (long long i = 0; i < n; ++i)
         out[i] = (sphx::lt_pos(x[i], sphx::kBitsHalf) ? 1 : 0) |
                  (sphx::abs_le(x[i], sphx::kBitsSeries) ? 2 : 0) | (sphx::gt_zero(x[i]) ? 4 : 0) |
                  (sphx::ge_zero(x[i]) ? 8 : 0) | (sphx::eq_zero(x[i]) ? 16 : 0) |
-                 (sphx::finite_bits(x[i]) ? 32 : 0);
+                 (sphx::finite_bits(x[i]) ? 32 : 0) | (sphx::le_zero(x[i]) ? 64 : 0);
 }

@@ -579,7 +579,7 @@ def test_fan_reciprocal_and_node_normalisation_on_the_host(pair_lib):
 
 def test_integer_comparisons_equal_the_fp64_ones(pair_lib):
     """The kernels test doubles on the integer pipe: x < 0.5, |x| <= 2^-9,
-    x > 0, x >= 0, x == 0 and isfinite(x) must equal the FP64 tests for signed
+    x > 0, x >= 0, x <= 0, x == 0 and isfinite(x) must equal the FP64 tests for signed
     zeros, subnormals, the constants and their neighbours, infinities, NaNs of
     either sign and random doubles over the whole exponent range."""
     import numpy as np
@@ -597,7 +597,8 @@ def test_integer_comparisons_equal_the_fp64_ones(pair_lib):
     with np.errstate(invalid="ignore"):
         want = ((x < 0.5).astype(int) | ((np.abs(x) <= 2.0 ** -9).astype(int) << 1)
                 | ((x > 0.0).astype(int) << 2) | ((x >= 0.0).astype(int) << 3)
-                | ((x == 0.0).astype(int) << 4) | (np.isfinite(x).astype(int) << 5))
+                | ((x == 0.0).astype(int) << 4) | (np.isfinite(x).astype(int) << 5)
+                | ((x <= 0.0).astype(int) << 6))
     assert np.array_equal(out, want)
 
 
