@@ -60,7 +60,15 @@ STRESS_WORKLOAD = ("ill-conditioned FP64-EFT stress, 10^6 arcs: 40% short (log-u
 MODES = ("wide", "eft", "direct", "ff32")
 # algorithmic work per arc of the dense call (both roots and the on-arc test)
 BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
-FP64_OPS_PER_ARC = {"eft": 465, "direct": 70}  # one op = add/mul/fma/div/sqrt
+# FP64 and FP32 thread instructions per arc of each mode's dense kernel (DFMA,
+# DADD and DMUL; FFMA, FADD and FMUL; the division and square-root sequences
+# counted by the instructions they expand to), from one ncu capture of 10^7
+# mixed arcs: properties of the compiled kernels, tagged with the capture
+OPS_SOURCE = ("ncu sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,ffma,fadd,fmul}_pred_on.sum "
+              "/ arcs, 10^7 arcs of the mixed workload, profiles/dense_modes_fp_ops_mixed_1e7.md "
+              "(kernels as of commit c24f7e5)")
+FP64_OPS_PER_ARC = {"eft": 446.5, "direct": 106.0, "ff32": 18.0, "wide": 14.0}
+FP32_OPS_PER_ARC = {"ff32": 176.0, "wide": 57.0}
 # Thread instructions per arc of dense_kernel<WIDE>, from one ncu capture
 # (smsp__inst_executed.sum x 32 / arcs): a property of the compiled kernel,
 # valid only for the build it was taken on, reported as a secondary figure.
@@ -458,8 +466,13 @@ def main():
                        "arcs_per_s": world * n / (ms * 1e-3), "hits_per_step": h,
                        "hbm_frac": BYTES_PER_ARC * n / (ms * 1e-3) / 1e9 / hbm_peak,
                        "error": ERROR[mode]}
+        # the FP64 and FP32 pipes' rooflines: ops per arc x arcs/s against the
+        # probes' FMA rates (one op per slot), with the source of the op counts
         if mode in FP64_OPS_PER_ARC:
             modes[mode]["fp64_pipe_frac"] = FP64_OPS_PER_ARC[mode] * n / (ms * 1e-3) / fp64_peak
+        if mode in FP32_OPS_PER_ARC:
+            modes[mode]["fp32_pipe_frac"] = FP32_OPS_PER_ARC[mode] * n / (ms * 1e-3) / fp32_peak
+        modes[mode]["ops_source"] = OPS_SOURCE
     value = modes[head]["value"]
     if e2e is not None:
         e2e["value"] = reduce_sum(e2e["hits_per_step"], dev) / (e2e["ms_per_step"] * 1e-3)
