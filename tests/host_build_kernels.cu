@@ -301,3 +301,8 @@ extern "C" void h_compares(const double *x, long long n, int *out) {
                  (sphx::ge_zero(x[i]) ? 8 : 0) | (sphx::eq_zero(x[i]) ? 16 : 0) |
                  (sphx::finite_bits(x[i]) ? 32 : 0) | (sphx::le_zero(x[i]) ? 64 : 0);
 }
+
+// the FP64 TwoSum the kernels use (magnitude-ordered FastTwoSum)
+extern "C" void h_two_sum(const double *a, const double *b, long long n, double *s, double *e) {
+    for (long long i = 0; i < n; ++i) sphx::two_sum<double>(a[i], b[i], s[i], e[i]);
+}

@@ -212,6 +212,7 @@ def pair_lib():
     L.h_rcp_den.argtypes = [vp, ll, vp]
     L.h_unit.argtypes = [vp, ll, vp]
     L.h_compares.argtypes = [vp, ll, vp]
+    L.h_two_sum.argtypes = [vp, vp, ll, vp, vp]
     L.h_searches.argtypes = [vp, ll, vp, ll, vp, vp, vp]
     L.h_to_fixed.argtypes = [vp, ll, vp, vp, vp]
     L.h_from_fixed.argtypes = [vp, vp, ll, vp]
@@ -329,16 +330,29 @@ def test_fast_fp32_conversion_equals_general_one(pair_lib):
 
 
 @pytest.mark.parametrize("form", ["accux", "accux_printed", "direct"])
-@pytest.mark.parametrize("gen", ["uniform", "stress"])
+@pytest.mark.parametrize("gen", ["uniform", "stress", "axes"])
 def test_fp64_forms_on_the_host_equal_step_reference(pair_lib, form, gen):
     """AccuX (renormalised and as printed) and direct FP64, the kernels' source
     built for the host, equal the step-by-step FP64 reference bit for bit: the
-    same correctly rounded operations in the same order."""
+    same correctly rounded operations in the same order (TwoSum in its
+    three-operation ordered form gives the same pairs). "axes" draws the
+    endpoint coordinates and z0 from 0, -0, +-1/2, +-1 and random values, so
+    that exact zeros, signed zeros and exact sums run through every step."""
     import numpy as np
     from oracle import steps
     from paper_2510_09892_gb300 import workloads as W
     from tests import parity as P
-    A, B, z = W.uniform_arcs(3000, seed=98) if gen == "uniform" else W.stress_arcs(3000, seed=99)
+    if gen == "axes":
+        rng = np.random.default_rng(112)
+        vals = np.array([0.0, -0.0, 0.5, -0.5, 1.0, -1.0])
+        A = np.where(rng.random((3000, 3)) < 0.6, rng.choice(vals, (3000, 3)),
+                     rng.standard_normal((3000, 3)))
+        B = np.where(rng.random((3000, 3)) < 0.6, rng.choice(vals, (3000, 3)),
+                     rng.standard_normal((3000, 3)))
+        z = np.where(rng.random(3000) < 0.5, rng.choice(vals, 3000), rng.uniform(-1, 1, 3000))
+    else:
+        A, B, z = (W.uniform_arcs(3000, seed=98) if gen == "uniform"
+                   else W.stress_arcs(3000, seed=99))
     A, B, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (A, B, z))
     n = len(z)
     pts = np.empty((n, 2, 3))
@@ -600,6 +614,45 @@ def test_integer_comparisons_equal_the_fp64_ones(pair_lib):
                 | ((x == 0.0).astype(int) << 4) | (np.isfinite(x).astype(int) << 5)
                 | ((x <= 0.0).astype(int) << 6))
     assert np.array_equal(out, want)
+
+
+def test_fp64_two_sum_equals_knuths_six_operations(pair_lib):
+    """The kernels' FP64 TwoSum (operands ordered by magnitude on the integer
+    pipe, then FastTwoSum) gives the pair of Knuth's six-operation TwoSum bit
+    for bit: random doubles over the whole exponent range, signed zeros,
+    subnormals, exact sums, equal and opposite operands and near-cancelling
+    ones. A planted mistake (the ordering reversed) must be caught."""
+    import numpy as np
+    rng = np.random.default_rng(111)
+    n = 400_000
+    def draw(k):
+        kind = rng.integers(0, 6, k)
+        v = rng.standard_normal(k) * 10.0 ** rng.uniform(-300, 300, k)
+        v = np.where(kind == 0, 0.0, v)
+        v = np.where(kind == 1, -0.0, v)
+        v = np.where(kind == 2, rng.choice([5e-324, -5e-324, 2.2e-308, -1e-310], k), v)
+        v = np.where(kind == 3, np.round(rng.standard_normal(k) * 8) / 8, v)
+        return v
+    a, b = draw(n), draw(n)
+    q = n // 10
+    b[:q] = -a[:q] * (1 + rng.standard_normal(q) * 1e-15)
+    b[q:2 * q] = a[q:2 * q]
+    b[2 * q:3 * q] = -a[2 * q:3 * q]
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    with np.errstate(all="ignore"):
+        x = a + b
+        bv = x - a
+        av = x - bv
+        e_ref = (a - av) + (b - bv)
+        # the ordering reversed (smaller operand first) must differ somewhere
+        small_first = np.abs(a) < np.abs(b)
+        xs, ys = np.where(small_first, a, b), np.where(small_first, b, a)
+        wrong = ys - ((xs + ys) - xs)
+    s, e = np.empty(n), np.empty(n)
+    pair_lib.h_two_sum(a.ctypes.data, b.ctypes.data, n, s.ctypes.data, e.ctypes.data)
+    assert np.array_equal(s.view(np.uint64), x.view(np.uint64))
+    assert np.array_equal(e.view(np.uint64), e_ref.view(np.uint64))
+    assert not np.array_equal(wrong.view(np.uint64), e_ref.view(np.uint64))
 
 
 def test_latitude_searches_on_the_host(pair_lib):
