@@ -66,8 +66,8 @@ BYTES_PER_ARC = 7 * 8 + 6 * 8 + 4   # 56 B in, 48 B points + 4 B count out
 # mixed arcs: properties of the compiled kernels, tagged with the capture
 OPS_SOURCE = ("ncu sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,ffma,fadd,fmul}_pred_on.sum "
               "/ arcs, 10^7 arcs of the mixed workload, profiles/dense_modes_fp_ops_mixed_1e7.md "
-              "(kernels as of commit c24f7e5)")
-FP64_OPS_PER_ARC = {"eft": 446.5, "direct": 106.0, "ff32": 18.0, "wide": 14.0}
+              "(kernels as of commit 4ff5d7b)")
+FP64_OPS_PER_ARC = {"eft": 413.5, "direct": 106.0, "ff32": 18.0, "wide": 14.0}
 FP32_OPS_PER_ARC = {"ff32": 176.0, "wide": 57.0}
 # Thread instructions per arc of dense_kernel<WIDE>, from one ncu capture
 # (smsp__inst_executed.sum x 32 / arcs): a property of the compiled kernel,
