@@ -308,9 +308,10 @@ sphx_status sphx_band_ranges(sphx_context *ctx, const double *nodes, int64_t n_n
    area, a fan of spherical triangles (Van Oosterom and Strackee's excess);
    cells cut by one latitude get the fan above their two crossings plus the
    sliver under the latitude arc; the rest take the boundary integral. The
-   cell lists live in ctx's scratch (allocated when a call needs more, then
-   kept; calls on one context must not overlap in time). mode: any
-   sphx_mode. Stream ordered. */
+   cell lists and a normalised copy of the nodes (24 B per node, made once per
+   call) live in ctx's scratch (allocated when a call needs more, then kept;
+   calls on one context must not overlap in time). mode: any sphx_mode but
+   SPHX_MODE_ADAPTIVE (SPHX_ERR_UNSUPPORTED). Stream ordered. */
 sphx_status sphx_band_areas(sphx_context *ctx, const double *nodes, int64_t n_nodes,
                             const int64_t *face_offsets, const int32_t *face_nodes,
                             int64_t n_face_nodes, int64_t n_faces, const double *lat_z,
