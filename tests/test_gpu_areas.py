@@ -142,6 +142,21 @@ def test_cubed_sphere_vs_oracle_and_partition(ctx, N):
     np.testing.assert_allclose(D.sum(axis=0), TWO_PI * np.diff(lat), rtol=0, atol=1e-14)
 
 
+def test_scaled_nodes_vs_oracle(ctx):
+    """Nodes are directions of any nonzero length: the same polygons with every
+    node scaled by 10^-3 .. 10^3 (the normalisation's reciprocal-square-root
+    path) and by 1 + up to 2^-22 (its series path) match the oracle, which
+    normalises the nodes itself."""
+    nodes, off, fn = W.polygon_cells(60, seed=34, radius=(1e-3, 0.5))
+    rng = np.random.default_rng(35)
+    half = len(nodes) // 2
+    scale = np.concatenate([10.0 ** rng.uniform(-3, 3, half),
+                            1 + rng.uniform(-2.0 ** -22, 2.0 ** -22, len(nodes) - half)])
+    nodes = np.ascontiguousarray(nodes * scale[:, None])
+    cells = W.cells_as_lists(nodes, off, fn)
+    check_against_oracle(ctx, cells, W.latlon_latitudes(91))
+
+
 def test_special_cells_vs_oracle(ctx):
     cells = special_cells()
     check_against_oracle(ctx, cells, W.latlon_latitudes(19))
